@@ -1,0 +1,453 @@
+#!/usr/bin/env python
+"""Benchmark: TSMTTSM percent of roofline over the width sweep at K = 2^24.
+
+One step = the whole sweep of plain-FP64 TSMTTSM calls (real with op T and
+complex with op C, alpha = 1, beta = 0) at K = 2^24 rows for
+M = N in {1, 2, 4, 8, 16, 32, 64} and (M, N) in {(1,64), (64,1), (8,32),
+(32,8)}: 22 kernel launches on inputs already resident in HBM.
+
+Roofline per call (Sec. 1.3, Eq. 1): flops = 2MNK (real) or 8MNK (complex),
+bytes = 8c(MK + NK + MN) (c = 2 for complex), P_max = min(I * b_s, P_fp64)
+with b_s the measured HBM bandwidth (MEASURED_PEAKS.json) and P_fp64 the
+larger of the nominal GB300 FP64 rate and the rate the DFMA probe measures
+live.  The reported value is whole-sweep efficiency:
+100 * sum(ideal time) / sum(measured time).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       python bench.py --case c64:64x64 --k 1048576   (one kernel, for profiling)
+"""
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+K_FULL = 1 << 24
+SQUARE = (1, 2, 4, 8, 16, 32, 64)
+OFFDIAG = ((1, 64), (64, 1), (8, 32), (32, 8))
+SWEEP = [(c, m, n) for c in (False, True) for (m, n) in [(w, w) for w in SQUARE] + list(OFFDIAG)]
+FP64_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 (vector and tensor), per GPU
+HBM_FALLBACK_GBS = 6800.0
+WORKLOAD = ("TSMTTSM FP64 sweep, K=2^24, real (op T) + complex (op C), M=N in {1,2,4,8,16,32,64} "
+            "+ (M,N) in {(1,64),(64,1),(8,32),(32,8)}, alpha=1, beta=0, row-major, ld=width, "
+            "uniform(-1,1) SplitMix64 inputs (A seed 0, B seed 1)")
+
+
+def model(cplx, M, N, K):
+    """(flops, bytes) of one TSMTTSM call with beta = 0 (Eq. 1 of the paper,
+    complex: 4x flops, 2x bytes)."""
+    c = 2 if cplx else 1
+    flops = 2.0 * M * N * K * (4 if cplx else 1)
+    nbytes = 8.0 * c * (M * K + N * K + M * N)
+    return flops, nbytes
+
+
+def ideal_seconds(cplx, M, N, K, bw_gbs, p64_gflops):
+    flops, nbytes = model(cplx, M, N, K)
+    return max(nbytes / (bw_gbs * 1e9), flops / (p64_gflops * 1e9))
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        loaded = [s for s in sm if s and s > 0.5 * (max(sm) if sm else 1)]
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            for i, n in enumerate(names):
+                if r[5 + i].lower().startswith("active"):
+                    reasons.add(n)
+        power = [num(r[3]) for r in rows if num(r[3]) is not None]
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------------ helpers
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1905_03136_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+    with open(os.path.join(ROOT, "paper_1905_03136_gb300", "codegen.py"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_for(variant_name, cfg_key):
+    """DRAM bytes per launch from a committed ncu capture, if it was taken on
+    the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    e = d.get(cfg_key)
+    if not e or e.get("source_hash") != _kernel_source_hash() or e.get("variant") != variant_name:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def _views(flatA, flatB, cplx, M, N, K):
+    import torch
+    c = 2 if cplx else 1
+    a = flatA[: K * M * c]
+    b = flatB[: K * N * c]
+    if cplx:
+        a = a.view(torch.complex128)
+        b = b.view(torch.complex128)
+    return a.view(K, M), b.view(K, N)
+
+
+def cpu_oracle_sweep(K_sample, K_full, bw, p64):
+    """Times the CPU oracle (single thread, as it stands) on the first
+    K_sample rows of every sweep configuration; returns (value, seconds,
+    per-config list) with times scaled linearly to K_full rows."""
+    import numpy as np
+    import oracle
+    import synth
+    total_ideal = 0.0
+    total_cpu = 0.0
+    wall = 0.0
+    for (cplx, M, N) in SWEEP:
+        A = synth.block_vector(synth.SEED_A, K_sample, M, complex_=cplx)
+        B = synth.block_vector(synth.SEED_B, K_sample, N, complex_=cplx)
+        C = np.zeros((M, N), dtype=A.dtype)
+        t0 = time.perf_counter()
+        oracle.tsmttsm("C" if cplx else "T", M, N, K_sample, 1.0, A, M, B, N, 0.0, C, N)
+        dt = time.perf_counter() - t0
+        wall += dt
+        total_cpu += dt * K_full / K_sample
+        total_ideal += ideal_seconds(cplx, M, N, K_full, bw, p64)
+    return 100.0 * total_ideal / total_cpu, wall
+
+
+# ------------------------------------------------------------------ arms
+
+def run_reference(args, bw, bw_src):
+    """The oracle as the reference arm: each step a bounded sample of the
+    sweep on the host (single-threaded C oracle)."""
+    p64 = FP64_NOMINAL_GFLOPS
+    K_s = args.ref_rows
+    for _ in range(args.warmup):
+        cpu_oracle_sweep(K_s, K_FULL, bw, p64)
+    vals, walls = [], []
+    for _ in range(args.steps):
+        v, w = cpu_oracle_sweep(K_s, K_FULL, bw, p64)
+        vals.append(v)
+        walls.append(w)
+    value = statistics.mean(vals)
+    sample = "first %d of 2^24 rows of each of the 22 sweep configurations, times scaled x%d" % (K_s, K_FULL // K_s)
+    line = {"impl": "reference", "metric": "TSMTTSM % of roofline vs width, K=2^24", "value": value,
+            "unit": "% of roofline", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(walls), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (SplitMix64 seeded)",
+            "config": {"workload": WORKLOAD, "K": K_FULL, "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": "% of roofline", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "% of roofline", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "peaks": {"hbm_gbs": bw, "hbm_source": bw_src, "fp64_gflops": p64, "fp64_source": "nominal"}}
+    print(json.dumps(line), flush=True)
+
+
+def run_case(args):
+    """One configuration, a few calls: the small case for ncu captures."""
+    import torch
+    import paper_1905_03136_gb300 as tsm
+    tsm.load()
+    kind, shape = args.case.split(":")
+    M, N = (int(x) for x in shape.split("x"))
+    cplx = kind == "c64"
+    c = 2 if cplx else 1
+    K = args.k
+    fa = torch.empty(K * M * c, dtype=torch.float64, device="cuda")
+    fb = torch.empty(K * N * c, dtype=torch.float64, device="cuda")
+    tsm.fill_random(fa.view(1, -1), 0)
+    tsm.fill_random(fb.view(1, -1), 1)
+    A, B = _views(fa, fb, cplx, M, N, K)
+    C = torch.zeros((M, N), dtype=A.dtype, device="cuda")
+    for _ in range(args.steps):
+        if args.split:
+            from paper_1905_03136_gb300 import split
+            split.tsmttsm_split(A, B, C, op="C" if cplx else "T")
+        else:
+            tsm.tsmttsm(A, B, C, op="C" if cplx else "T")
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.case, "K": K, "ok": True}))
+
+
+def run_ours(args, bw, bw_src):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_1905_03136_gb300 as tsm
+    from paper_1905_03136_gb300 import probe
+    tsm.load()
+    dev = torch.device("cuda", local)
+    K = K_FULL
+
+    # Inputs: one flat buffer per operand, seeded once (outside timing).
+    flatA = torch.empty(K * 128, dtype=torch.float64, device=dev)
+    flatB = torch.empty(K * 128, dtype=torch.float64, device=dev)
+    tsm.fill_random(flatA.view(K, 128), 0)
+    tsm.fill_random(flatB.view(K, 128), 1)
+    outs = {cfg: torch.zeros((cfg[1], cfg[2]), dtype=torch.complex128 if cfg[0] else torch.float64, device=dev)
+            for cfg in SWEEP}
+    views = {cfg: _views(flatA, flatB, cfg[0], cfg[1], cfg[2], K) for cfg in SWEEP}
+    chosen = {cfg: tsm.choose(tsm.KIND_TSMTTSM, tsm.C64 if cfg[0] else tsm.R64, cfg[1], cfg[2], K) for cfg in SWEEP}
+    names = {v["index"]: v["name"] for v in tsm.variants(tsm.KIND_TSMTTSM)}
+
+    dfma = probe.fp64_peak(0)
+    dmma = probe.fp64_peak(1)
+    p64 = max(FP64_NOMINAL_GFLOPS, dfma, dmma)
+    p64_src = "nominal" if p64 == FP64_NOMINAL_GFLOPS else ("measured DFMA probe" if p64 == dfma else
+                                                             "measured DMMA probe")
+
+    stream = torch.cuda.current_stream()
+
+    def step(record=None):
+        for cfg in SWEEP:
+            A, B = views[cfg]
+            if record is not None:
+                record[cfg][0].record(stream)
+            tsm.tsmttsm(A, B, outs[cfg], op="C" if cfg[0] else "T")
+            if record is not None:
+                record[cfg][1].record(stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+
+    events = [{cfg: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for cfg in SWEEP} for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    t_start.record(stream)
+    for s in range(args.steps):
+        step(events[s])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clock_info = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    per_cfg = {cfg: statistics.mean(events[s][cfg][0].elapsed_time(events[s][cfg][1]) for s in range(args.steps))
+               for cfg in SWEEP}
+
+    ideal = {cfg: ideal_seconds(cfg[0], cfg[1], cfg[2], K, bw, p64) for cfg in SWEEP}
+    ms_step = total_ms / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = 100.0 * sum(ideal.values()) / (ms_step * 1e-3)
+
+    sweep = []
+    for cfg in SWEEP:
+        flops, nbytes = model(cfg[0], cfg[1], cfg[2], K)
+        ms = per_cfg[cfg]
+        bound = "fp64" if flops / (p64 * 1e9) >= nbytes / (bw * 1e9) else "hbm"
+        sweep.append({"dtype": "c64" if cfg[0] else "r64", "M": cfg[1], "N": cfg[2], "ms": round(ms, 4),
+                      "gflops": round(flops / (ms * 1e-3) / 1e9, 2), "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                      "roofline_pct": round(100.0 * ideal[cfg] / (ms * 1e-3), 2), "bound": bound,
+                      "variant": names[chosen[cfg][0]], "grid": chosen[cfg][1]})
+
+    # Dominant kernel: the longest call of the step.
+    dom = max(SWEEP, key=lambda c: per_cfg[c])
+    flops, nbytes = model(dom[0], dom[1], dom[2], K)
+    dom_ms = per_cfg[dom]
+    fp64_bound = flops / (p64 * 1e9) >= nbytes / (bw * 1e9)
+    if fp64_bound:
+        achieved = flops / (dom_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": p64 / 1e3, "unit": "TFLOP/s",
+                "frac": achieved / (p64 / 1e3), "peak_source": "FP64 pipe, " + p64_src}
+    else:
+        achieved = nbytes / (dom_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": bw, "unit": "GB/s", "frac": achieved / bw,
+                "peak_source": bw_src}
+    cfg_key = "%s:%dx%d" % ("c64" if dom[0] else "r64", dom[1], dom[2])
+    roof["traffic"] = _traffic_for(names[chosen[dom][0]], cfg_key)
+    roof["kernel"] = names[chosen[dom][0]]
+    roof["config"] = cfg_key
+
+    # End to end: host (pinned) inputs copied in and C copied out every call.
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, flatA, flatB, outs, views, ideal, dev, K)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, wall = cpu_oracle_sweep(args.cpu_rows, K, bw, p64)
+        cpu = {"value": v, "unit": "% of roofline", "cores": 1, "kind": "oracle",
+               "sample": "first %d of 2^24 rows of each of the 22 sweep configurations (%.1f s of CPU), "
+                         "times scaled x%d" % (args.cpu_rows, wall, K // args.cpu_rows)}
+
+    if rank == 0:
+        line = {"metric": "TSMTTSM % of roofline vs width, K=2^24", "value": value, "unit": "% of roofline",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (SplitMix64 seeded, generated on device)",
+                "config": {"workload": WORKLOAD, "K": K, "calls_per_step": len(SWEEP),
+                           "l2": "inputs 2^24 rows >> 129 MB L2 except the C outputs; no flush",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "gpu_launches": len(SWEEP) * args.steps,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clock_info,
+                "peaks": {"hbm_gbs": bw, "hbm_source": bw_src, "fp64_gflops_used": p64,
+                          "fp64_source": p64_src, "fp64_nominal_gflops": FP64_NOMINAL_GFLOPS,
+                          "dfma_probe_gflops": dfma, "dmma_probe_gflops": dmma},
+                "sweep": sweep}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_e2e(args, flatA, flatB, outs, views, ideal, dev, K):
+    """One sweep where every call first copies its A and B from pinned host
+    memory and reads C back: the same metric measured end to end."""
+    import torch
+    try:
+        hA = torch.empty(flatA.numel(), dtype=torch.float64, pin_memory=True)
+        hB = torch.empty(flatB.numel(), dtype=torch.float64, pin_memory=True)
+        pinned = True
+    except Exception:
+        hA = torch.empty(flatA.numel(), dtype=torch.float64)
+        hB = torch.empty(flatB.numel(), dtype=torch.float64)
+        pinned = False
+    hA.copy_(flatA)
+    hB.copy_(flatB)
+    dA = torch.empty_like(flatA)
+    dB = torch.empty_like(flatB)
+    hC = {cfg: torch.empty(outs[cfg].shape, dtype=outs[cfg].dtype, pin_memory=pinned) for cfg in SWEEP}
+    import paper_1905_03136_gb300 as tsm
+    h2d = d2h = 0
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for cfg in SWEEP:
+        cplx, M, N = cfg
+        c = 2 if cplx else 1
+        na, nb = K * M * c, K * N * c
+        dA[:na].copy_(hA[:na], non_blocking=True)
+        dB[:nb].copy_(hB[:nb], non_blocking=True)
+        A, B = _views(dA, dB, cplx, M, N, K)
+        tsm.tsmttsm(A, B, outs[cfg], op="C" if cplx else "T")
+        hC[cfg].copy_(outs[cfg], non_blocking=True)
+        h2d += 8 * (na + nb)
+        d2h += outs[cfg].numel() * outs[cfg].element_size()
+    t1.record()
+    torch.cuda.synchronize()
+    secs = t0.elapsed_time(t1) * 1e-3
+    del dA, dB, hA, hB
+    torch.cuda.empty_cache()
+    return {"value": 100.0 * sum(ideal.values()) / secs, "unit": "% of roofline", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": secs * 1e3, "pinned": pinned}
+
+
+def main():
+    ap = argparse.ArgumentParser(description="TSMTTSM roofline sweep benchmark")
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--cpu-rows", type=int, default=1 << 17, help="rows of the CPU-oracle sample per config")
+    ap.add_argument("--ref-rows", type=int, default=1 << 14, help="rows per config per reference-arm step")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--case", default=None, help="profile one config, e.g. c64:64x64")
+    ap.add_argument("--k", type=int, default=1 << 20, help="rows for --case")
+    ap.add_argument("--split", action="store_true", help="--case: use the split-precision path")
+    args = ap.parse_args()
+    bw, bw_src = load_peaks()
+    if args.case:
+        return run_case(args)
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        return run_reference(args, bw, bw_src)
+    return run_ours(args, bw, bw_src)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,369 @@
+"""Code generator for width-specialised FP64 kernels (Sec. 2.1 of the paper).
+
+Like the paper's generator, this script writes CUDA source for fixed sizes:
+every loop over the small dimensions is unrolled into straight-line code
+with one named scalar per accumulator (Listing 3), index arithmetic uses
+compile-time constants, and guards are emitted only for the tile entries
+that can cross the matrix border (entries that every thread owns inside the
+matrix get none).  The kernels reuse the hand-written deterministic
+reduction epilogue and C staging from ``csrc/fp64_common.cuh``.
+
+Generated kernels register themselves in the library's variant table with
+``fixed_m``/``fixed_n`` set, so dispatch and the autotuner only offer them for
+their own shape.  The default variant set covers the widths of the
+benchmark sweep (M = N in powers of two up to 64 plus four off-diagonal
+pairs) with a few tile / threads-per-row choices each; ``--specs`` adds more.
+
+Usage:  python -m paper_1905_03136_gb300.codegen OUT_DIR [--shards N]
+"""
+
+import argparse
+import math
+import os
+
+SWEEP_SQUARE = (1, 2, 4, 8, 16, 32, 64)
+SWEEP_OFFDIAG = ((1, 64), (64, 1), (8, 32), (32, 8))
+TSMM_OFFDIAG = ((4, 64), (64, 4))
+BLOCK = 256
+
+
+def _tiles_for(M, N, cplx):
+    """Up to three register tiles (T_M, T_N) for a TSMTTSM shape, preferring
+    divisors of M and N (no guards, no idle threads; Sec. 5.2) and tiles whose
+    thread count P = ceil(M/T_M) ceil(N/T_N) fits one CTA."""
+    cap = 16 if cplx else 32          # accumulators per thread (doubles)
+    cands = []
+    for tm in (1, 2, 4, 8, 16):
+        for tn in (1, 2, 4, 8, 16):
+            if tm > M or tn > N:
+                continue
+            acc = tm * tn * (2 if cplx else 1)
+            if acc > cap:
+                continue
+            P = math.ceil(M / tm) * math.ceil(N / tn)
+            if P > BLOCK:
+                continue
+            divides = (M % tm == 0) and (N % tn == 0)
+            squareness = -abs(math.log2(tm) - math.log2(tn))
+            cands.append((divides, tm * tn, squareness, tm, tn))
+    cands.sort(reverse=True)
+    out = []
+    for c in cands:
+        if (c[3], c[4]) not in out:
+            out.append((c[3], c[4]))
+        if len(out) == 3:
+            break
+    return out
+
+
+def default_specs():
+    tsmttsm, tsmm = [], []
+    shapes = [(w, w) for w in SWEEP_SQUARE] + list(SWEEP_OFFDIAG)
+    for cplx in (False, True):
+        for (M, N) in shapes:
+            for (tm, tn) in _tiles_for(M, N, cplx):
+                U = 4 if tm * tn <= 2 else (2 if tm * tn <= 8 else 1)
+                tsmttsm.append(dict(cplx=cplx, M=M, N=N, TM=tm, TN=tn, U=U))
+    tshapes = [(w, w) for w in SWEEP_SQUARE] + list(TSMM_OFFDIAG)
+    for cplx in (False, True):
+        for (M, N) in tshapes:
+            tprs = sorted({min(t, N) for t in (4, 8, 16)})
+            for tpr in tprs:
+                npt = math.ceil(N / tpr)
+                U = 2 if npt * (2 if cplx else 1) <= 8 else 1
+                tsmm.append(dict(cplx=cplx, M=M, N=N, TPR=tpr, U=U))
+    return tsmttsm, tsmm
+
+
+def _name_tsmttsm(s):
+    return "gen_tsmttsm_%s_m%dn%d_t%dx%d_u%d" % ("c64" if s["cplx"] else "r64", s["M"], s["N"],
+                                                 s["TM"], s["TN"], s["U"])
+
+
+def _name_tsmm(s):
+    return "gen_tsmm_%s_m%dn%d_tpr%d_u%d" % ("c64" if s["cplx"] else "r64", s["M"], s["N"],
+                                             s["TPR"], s["U"])
+
+
+def emit_tsmttsm(s):
+    """One TSMTTSM kernel for fixed M, N, tile and unroll."""
+    M, N, TM, TN, U, cplx = s["M"], s["N"], s["TM"], s["TN"], s["U"], s["cplx"]
+    CC = 2 if cplx else 1
+    PM, PN = math.ceil(M / TM), math.ceil(N / TN)
+    P = PM * PN
+    L = BLOCK // P
+    name = _name_tsmttsm(s)
+    # entry i is always in range iff the largest pm (PM - 1) still fits
+    gm = [(PM - 1) + i * PM >= M for i in range(TM)]
+    gn = [(PN - 1) + j * PN >= N for j in range(TN)]
+    o = []
+    w = o.append
+    w("template <bool CONJ>")
+    w("__global__ void __launch_bounds__(%d) %s(const TsmttsmArgs a) {" % (BLOCK, name))
+    w("    constexpr int PM = %d, PN = %d, P = %d, L = %d;" % (PM, PN, P, L))
+    w("    const int t = threadIdx.x;")
+    w("    const int lane = t / P, p = t - lane * P;")
+    w("    const int pm = p % PM, pn = p / PM;")
+    w("    const bool active = %s;" % ("lane < L" if L * P < BLOCK else "true"))
+    for i in range(TM):
+        if gm[i]:
+            w("    const bool gm%d = pm + %d < %d;" % (i, i * PM, M))
+    for j in range(TN):
+        if gn[j]:
+            w("    const bool gn%d = pn + %d < %d;" % (j, j * PN, N))
+    for i in range(TM):
+        for j in range(TN):
+            for c in range(CC):
+                w("    double c%d_%d_%d = 0.0;" % (i, j, c))
+    w("    const int64_t G = gridDim.x;")
+    w("    const int64_t k0 = a.K * (int64_t)blockIdx.x / G;")
+    w("    const int64_t k1 = a.K * ((int64_t)blockIdx.x + 1) / G;")
+    w("    const double* __restrict__ Ab = a.A + pm * %d;" % CC)
+    w("    const double* __restrict__ Bb = a.B + pn * %d;" % CC)
+    w("    const int64_t sa = a.lda * %d, sb = a.ldb * %d;" % (CC, CC))
+
+    def body(rows):
+        lines = []
+        for u in range(rows):
+            off = "" if u == 0 else " + (int64_t)%d * L" % u
+            lines.append("            const double* ar%d = Ab + (k%s) * sa;" % (u, off))
+            lines.append("            const double* br%d = Bb + (k%s) * sb;" % (u, off))
+        for u in range(rows):
+            for i in range(TM):
+                for c in range(CC):
+                    ld = "__ldg(ar%d + %d)" % (u, i * PM * CC + c)
+                    if gm[i]:
+                        ld = "gm%d ? %s : 0.0" % (i, ld)
+                    lines.append("            const double a%d_%d_%d = %s;" % (u, i, c, ld))
+            for j in range(TN):
+                for c in range(CC):
+                    ld = "__ldg(br%d + %d)" % (u, j * PN * CC + c)
+                    if gn[j]:
+                        ld = "gn%d ? %s : 0.0" % (j, ld)
+                    lines.append("            const double b%d_%d_%d = %s;" % (u, j, c, ld))
+        for u in range(rows):
+            for i in range(TM):
+                for j in range(TN):
+                    guard = []
+                    if gm[i]:
+                        guard.append("gm%d" % i)
+                    if gn[j]:
+                        guard.append("gn%d" % j)
+                    pre = ("if (%s) " % " && ".join(guard)) if guard else ""
+                    if not cplx:
+                        lines.append("            %sc%d_%d_0 = fma(a%d_%d_0, b%d_%d_0, c%d_%d_0);"
+                                     % (pre, i, j, u, i, u, j, i, j))
+                    else:
+                        A_r, A_i = "a%d_%d_0" % (u, i), "a%d_%d_1" % (u, i)
+                        B_r, B_i = "b%d_%d_0" % (u, j), "b%d_%d_1" % (u, j)
+                        cr, ci = "c%d_%d_0" % (i, j), "c%d_%d_1" % (i, j)
+                        lines.append("            %s{" % pre)
+                        lines.append("                %s = fma(%s, %s, %s);" % (cr, A_r, B_r, cr))
+                        lines.append("                %s = fma(CONJ ? %s : -%s, %s, %s);" % (cr, A_i, A_i, B_i, cr))
+                        lines.append("                %s = fma(%s, %s, %s);" % (ci, A_r, B_i, ci))
+                        lines.append("                %s = fma(CONJ ? -%s : %s, %s, %s);" % (ci, A_i, A_i, B_r, ci))
+                        lines.append("            }")
+        return lines
+
+    w("    if (active) {")
+    w("        int64_t k = k0 + lane;")
+    if U > 1:
+        w("        for (; k + (int64_t)%d * L < k1; k += (int64_t)%d * L) {" % (U - 1, U))
+        o.extend(body(U))
+        w("        }")
+    w("        for (; k < k1; k += L) {")
+    o.extend(body(1))
+    w("        }")
+    w("    }")
+    accs = ", ".join("c%d_%d_%d" % (i, j, c) for i in range(TM) for j in range(TN) for c in range(CC))
+    w("    const double acc[%d] = {%s};" % (TM * TN * CC, accs))
+    w("    tsmttsm_finish<%d, %d, %d>(a, acc, PM, PN, L, lane, p, active);" % (TM, TN, CC))
+    w("}")
+    w("")
+    w("cudaError_t launch_%s(const TsmttsmArgs& a, int grid, cudaStream_t s) {" % name)
+    if cplx:
+        w("    if (a.conj) %s<true><<<grid, %d, 0, s>>>(a);" % (name, BLOCK))
+        w("    else %s<false><<<grid, %d, 0, s>>>(a);" % (name, BLOCK))
+    else:
+        w("    %s<false><<<grid, %d, 0, s>>>(a);" % (name, BLOCK))
+    w("    return cudaGetLastError();")
+    w("}")
+    w("int occ_%s(int, int) {" % name)
+    w("    int n = 0;")
+    w("    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, %s<false>, %d, 0) != cudaSuccess) return 0;"
+      % (name, BLOCK))
+    w("    return n;")
+    w("}")
+    w("")
+    return "\n".join(o)
+
+
+def emit_tsmm(s):
+    """One TSMM kernel for fixed M, N, threads per row and unroll; C comes
+    from shared memory (Sec. 4.2), the m loop is fully unrolled."""
+    M, N, TPR, U, cplx = s["M"], s["N"], s["TPR"], s["U"], s["cplx"]
+    CC = 2 if cplx else 1
+    NPT = math.ceil(N / TPR)
+    RPC = BLOCK // TPR
+    name = _name_tsmm(s)
+    gn = [(TPR - 1) + j * TPR >= N for j in range(NPT)]
+    o = []
+    w = o.append
+    w("__global__ void __launch_bounds__(%d) %s(const TsmmArgs a) {" % (BLOCK, name))
+    w("    extern __shared__ double cs[];")
+    w("    tsmm_stage_c<%d>(a, cs);" % CC)
+    w("    constexpr int TPR = %d, RPC = %d;" % (TPR, RPC))
+    w("    const int r = threadIdx.x / TPR, q = threadIdx.x - r * TPR;")
+    for j in range(NPT):
+        if gn[j]:
+            w("    const bool gn%d = q + %d < %d;" % (j, j * TPR, N))
+    w("    const int64_t sa = a.lda * %d, sb = a.ldb * %d;" % (CC, CC))
+    w("    const int64_t step = (int64_t)gridDim.x * RPC * %d;" % U)
+    w("    for (int64_t base = (int64_t)blockIdx.x * RPC * %d + r; base - r < a.K; base += step) {" % U)
+    for u in range(U):
+        w("        const bool rok%d = base + %d < a.K;" % (u, u * RPC))
+        w("        const double* ar%d = a.A + (rok%d ? base + %d : 0) * sa;" % (u, u, u * RPC))
+    for u in range(U):
+        for j in range(NPT):
+            for c in range(CC):
+                w("        double x%d_%d_%d = 0.0;" % (u, j, c))
+    for m in range(M):
+        for u in range(U):
+            for c in range(CC):
+                w("        const double a%d_%d_%d = rok%d ? __ldg(ar%d + %d) : 0.0;" % (u, m, c, u, u, m * CC + c))
+        for j in range(NPT):
+            guard = ("if (gn%d) " % j) if gn[j] else ""
+            w("        %s{" % guard)
+            for c in range(CC):
+                w("            const double c%d = cs[(%d * %d + q + %d) * %d + %d];" % (c, m, N, j * TPR, CC, c))
+            for u in range(U):
+                if not cplx:
+                    w("            x%d_%d_0 = fma(a%d_%d_0, c0, x%d_%d_0);" % (u, j, u, m, u, j))
+                else:
+                    w("            x%d_%d_0 = fma(a%d_%d_0, c0, x%d_%d_0);" % (u, j, u, m, u, j))
+                    w("            x%d_%d_0 = fma(-a%d_%d_1, c1, x%d_%d_0);" % (u, j, u, m, u, j))
+                    w("            x%d_%d_1 = fma(a%d_%d_0, c1, x%d_%d_1);" % (u, j, u, m, u, j))
+                    w("            x%d_%d_1 = fma(a%d_%d_1, c0, x%d_%d_1);" % (u, j, u, m, u, j))
+            w("        }")
+    for u in range(U):
+        w("        if (rok%d) {" % u)
+        w("            double* out = a.B + (base + %d) * sb;" % (u * RPC))
+        for j in range(NPT):
+            guard = ("if (gn%d) " % j) if gn[j] else ""
+            w("            %stsmm_store<%d>(a, out, q + %d, x%d_%d_0, x%d_%d_%d);"
+              % (guard, CC, j * TPR, u, j, u, j, CC - 1))
+        w("        }")
+    w("    }")
+    w("}")
+    w("")
+    smem = M * N * CC * 8
+    w("cudaError_t launch_%s(const TsmmArgs& a, int grid, cudaStream_t s) {" % name)
+    if smem > 48 * 1024:
+        w("    cudaError_t e = cudaFuncSetAttribute(%s, cudaFuncAttributeMaxDynamicSharedMemorySize, %d);"
+          % (name, smem))
+        w("    if (e != cudaSuccess) return e;")
+    w("    %s<<<grid, %d, %d, s>>>(a);" % (name, BLOCK, smem))
+    w("    return cudaGetLastError();")
+    w("}")
+    w("int occ_%s(int, int) {" % name)
+    if smem > 48 * 1024:
+        w("    if (cudaFuncSetAttribute(%s, cudaFuncAttributeMaxDynamicSharedMemorySize, %d) != cudaSuccess)"
+          " return 0;" % (name, smem))
+    w("    int n = 0;")
+    w("    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, %s, %d, %d) != cudaSuccess) return 0;"
+      % (name, BLOCK, smem))
+    w("    return n;")
+    w("}")
+    w("")
+    return "\n".join(o)
+
+
+HEADER = """// GENERATED by paper_1905_03136_gb300/codegen.py -- do not edit.
+#include <cstdio>
+#include <cstring>
+#include "fp64_common.cuh"
+#include "tsm_internal.h"
+namespace tsm {
+"""
+
+
+def _reg_tsmttsm(s):
+    name = _name_tsmttsm(s)
+    return ("    { Variant v; memset(&v, 0, sizeof(v)); snprintf(v.info.name, sizeof(v.info.name), \"%s\");"
+            " v.info.kind = TSM_KIND_TSMTTSM; v.info.dtype = %d; v.info.fixed_m = %d; v.info.fixed_n = %d;"
+            " v.info.tile_m = %d; v.info.tile_n = %d; v.info.unroll = %d; v.info.block = %d;"
+            " v.info.generated = 1; v.tsmttsm = launch_%s; v.occupancy = occ_%s; t.push_back(v); }"
+            % (name, 1 if s["cplx"] else 0, s["M"], s["N"], s["TM"], s["TN"], s["U"], BLOCK, name, name))
+
+
+def _reg_tsmm(s):
+    name = _name_tsmm(s)
+    npt = math.ceil(s["N"] / s["TPR"])
+    return ("    { Variant v; memset(&v, 0, sizeof(v)); snprintf(v.info.name, sizeof(v.info.name), \"%s\");"
+            " v.info.kind = TSM_KIND_TSMM; v.info.dtype = %d; v.info.fixed_m = %d; v.info.fixed_n = %d;"
+            " v.info.tile_n = %d; v.info.threads_per_row = %d; v.info.unroll = %d; v.info.block = %d;"
+            " v.info.generated = 1; v.tsmm = launch_%s; v.occupancy = occ_%s; m.push_back(v); }"
+            % (name, 1 if s["cplx"] else 0, s["M"], s["N"], npt, s["TPR"], s["U"], BLOCK, name, name))
+
+
+def generate(out_dir, shards=4, specs=None):
+    """Writes gen_shard{i}.cu (kernels) and gen_registry.cu; returns the list
+    of written files.  Files whose content is unchanged are not rewritten,
+    so incremental builds skip them."""
+    tsmttsm, tsmm = specs if specs is not None else default_specs()
+    os.makedirs(out_dir, exist_ok=True)
+    items = [("t", s) for s in tsmttsm] + [("m", s) for s in tsmm]
+    # balance shards by a rough code-size estimate
+    def cost(it):
+        k, s = it
+        if k == "t":
+            return s["TM"] * s["TN"] * s["U"] * (4 if s["cplx"] else 1) + 8
+        return s["M"] * math.ceil(s["N"] / s["TPR"]) * s["U"] * (4 if s["cplx"] else 1) + 8
+    bins = [[] for _ in range(shards)]
+    loads = [0] * shards
+    for it in sorted(items, key=cost, reverse=True):
+        b = loads.index(min(loads))
+        bins[b].append(it)
+        loads[b] += cost(it)
+    files = []
+    decls = []
+    for i, b in enumerate(bins):
+        src = [HEADER]
+        for k, s in b:
+            src.append(emit_tsmttsm(s) if k == "t" else emit_tsmm(s))
+        src.append("}  // namespace tsm\n")
+        files.append(_write(os.path.join(out_dir, "gen_shard%d.cu" % i), "\n".join(src)))
+    for s in tsmttsm:
+        n = _name_tsmttsm(s)
+        decls.append("cudaError_t launch_%s(const TsmttsmArgs&, int, cudaStream_t); int occ_%s(int, int);" % (n, n))
+    for s in tsmm:
+        n = _name_tsmm(s)
+        decls.append("cudaError_t launch_%s(const TsmmArgs&, int, cudaStream_t); int occ_%s(int, int);" % (n, n))
+    reg = [HEADER] + decls + ["void register_generated_variants(std::vector<Variant>& t, std::vector<Variant>& m) {"]
+    reg += [_reg_tsmttsm(s) for s in tsmttsm] + [_reg_tsmm(s) for s in tsmm]
+    reg += ["}", "}  // namespace tsm", ""]
+    files.append(_write(os.path.join(out_dir, "gen_registry.cu"), "\n".join(reg)))
+    return files
+
+
+def _write(path, text):
+    if os.path.exists(path):
+        with open(path) as f:
+            if f.read() == text:
+                return path
+    with open(path, "w") as f:
+        f.write(text)
+    return path
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("out_dir")
+    ap.add_argument("--shards", type=int, default=4)
+    args = ap.parse_args()
+    for f in generate(args.out_dir, args.shards):
+        print(f)
+
+
+if __name__ == "__main__":
+    main()

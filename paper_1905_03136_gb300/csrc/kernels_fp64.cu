@@ -1,0 +1,391 @@
+// Hand-written FP64 kernel families for TSMTTSM and TSMM (binary64 on the
+// FP64 pipe, no tensor cores).
+//
+// TSMTTSM (Sec. 3): the long K loop is split into one contiguous row range
+// per CTA; inside a CTA, P = ceil(M/T_M) * ceil(N/T_N) threads each own a
+// T_M x T_N register tile of C (Listing 5) and L = 256 / P row lanes walk the
+// range with stride L, U rows per iteration (the loads of U rows are issued
+// before their FMAs, which plays the role of the paper's leap frogging,
+// Sec. 3.1).  Tiles use the transposed mapping of Fig. 10: tile entry (i, j)
+// of thread (pm, pn) is C[pm + i*PM][pn + j*PN], so neighbouring threads load
+// neighbouring addresses.  Tile entries past M or N are guarded (Sec. 2.1).
+//
+// Reduction (Sec. 3.2, replaced by a deterministic scheme): lanes of a CTA
+// are summed through shared memory in lane order; each CTA writes its M x N
+// partial to a workspace; the last CTA to take a ticket sums the partials in
+// CTA order, applies alpha/beta and resets the ticket.  No floating-point
+// atomics, so results repeat bit for bit.
+//
+// TSMM (Sec. 4): alpha*C is staged once per CTA in shared memory (Sec. 4.2);
+// TPR threads share one row of B and each computes up to NPT results,
+// interleaved (Fig. 12) so that consecutive threads store consecutive
+// elements; U rows per thread per iteration reuse every C value U times
+// (Sec. 4.2, Fig. 13).  The grid is persistent (a multiple of the SM count)
+// and walks K with a grid stride.
+#include <cstdio>
+#include <cstring>
+
+#include "fp64_common.cuh"
+#include "tsm_internal.h"
+
+namespace tsm {
+namespace {
+
+// ------------------------------------------------------------------ TSMTTSM
+
+template <int TM, int TN, int U, bool CPLX, bool CONJ>
+__global__ void __launch_bounds__(kBlock) k_tsmttsm(const TsmttsmArgs a) {
+    constexpr int CC = CPLX ? 2 : 1;
+    const int M = a.M, N = a.N;
+    const int PM = (M + TM - 1) / TM, PN = (N + TN - 1) / TN, P = PM * PN;
+    const int L = kBlock / P;
+    const int t = threadIdx.x;
+    const int lane = t / P, p = t - lane * P;
+    const int pm = p % PM, pn = p / PM;
+    const bool active = lane < L;
+
+    int mi[TM], nj[TN];
+    bool mok[TM], nok[TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        mi[i] = pm + i * PM;
+        mok[i] = mi[i] < M;
+        if (!mok[i]) mi[i] = 0;
+    }
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+        nj[j] = pn + j * PN;
+        nok[j] = nj[j] < N;
+        if (!nok[j]) nj[j] = 0;
+    }
+
+    double acc[TM][TN][CC];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j)
+#pragma unroll
+            for (int c = 0; c < CC; ++c) acc[i][j][c] = 0.0;
+
+    const int64_t G = gridDim.x;
+    const int64_t k0 = a.K * (int64_t)blockIdx.x / G;
+    const int64_t k1 = a.K * ((int64_t)blockIdx.x + 1) / G;
+    const double* __restrict__ A = a.A;
+    const double* __restrict__ B = a.B;
+    const int64_t sa = a.lda * CC, sb = a.ldb * CC;
+
+    if (active) {
+        int64_t k = k0 + lane;
+        for (; k + (int64_t)(U - 1) * L < k1; k += (int64_t)U * L) {
+            double av[U][TM][CC], bv[U][TN][CC];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const double* ar = A + (k + (int64_t)u * L) * sa;
+                const double* br = B + (k + (int64_t)u * L) * sb;
+#pragma unroll
+                for (int i = 0; i < TM; ++i)
+#pragma unroll
+                    for (int c = 0; c < CC; ++c) av[u][i][c] = mok[i] ? __ldg(ar + mi[i] * CC + c) : 0.0;
+#pragma unroll
+                for (int j = 0; j < TN; ++j)
+#pragma unroll
+                    for (int c = 0; c < CC; ++c) bv[u][j][c] = nok[j] ? __ldg(br + nj[j] * CC + c) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int i = 0; i < TM; ++i)
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) {
+                        if (!CPLX) {
+                            acc[i][j][0] = fma(av[u][i][0], bv[u][j][0], acc[i][j][0]);
+                        } else {
+                            const double ar = av[u][i][0], ai = av[u][i][CC - 1];
+                            const double br = bv[u][j][0], bi = bv[u][j][CC - 1];
+                            acc[i][j][0] = fma(ar, br, acc[i][j][0]);
+                            acc[i][j][0] = fma(CONJ ? ai : -ai, bi, acc[i][j][0]);
+                            acc[i][j][CC - 1] = fma(ar, bi, acc[i][j][CC - 1]);
+                            acc[i][j][CC - 1] = fma(CONJ ? -ai : ai, br, acc[i][j][CC - 1]);
+                        }
+                    }
+        }
+        for (; k < k1; k += L) {
+            const double* ar = A + k * sa;
+            const double* br = B + k * sb;
+            double av[TM][CC], bv[TN][CC];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int c = 0; c < CC; ++c) av[i][c] = mok[i] ? __ldg(ar + mi[i] * CC + c) : 0.0;
+#pragma unroll
+            for (int j = 0; j < TN; ++j)
+#pragma unroll
+                for (int c = 0; c < CC; ++c) bv[j][c] = nok[j] ? __ldg(br + nj[j] * CC + c) : 0.0;
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) {
+                    if (!CPLX) {
+                        acc[i][j][0] = fma(av[i][0], bv[j][0], acc[i][j][0]);
+                    } else {
+                        const double ar_ = av[i][0], ai = av[i][CC - 1];
+                        const double br_ = bv[j][0], bi = bv[j][CC - 1];
+                        acc[i][j][0] = fma(ar_, br_, acc[i][j][0]);
+                        acc[i][j][0] = fma(CONJ ? ai : -ai, bi, acc[i][j][0]);
+                        acc[i][j][CC - 1] = fma(ar_, bi, acc[i][j][CC - 1]);
+                        acc[i][j][CC - 1] = fma(CONJ ? -ai : ai, br_, acc[i][j][CC - 1]);
+                    }
+                }
+        }
+    }
+
+    tsmttsm_finish<TM, TN, CC>(a, &acc[0][0][0], PM, PN, L, lane, p, active);
+}
+
+template <int TM, int TN, int U, bool CPLX>
+cudaError_t launch_tsmttsm(const TsmttsmArgs& a, int grid, cudaStream_t s) {
+    if (CPLX && a.conj)
+        k_tsmttsm<TM, TN, U, CPLX, true><<<grid, kBlock, 0, s>>>(a);
+    else
+        k_tsmttsm<TM, TN, U, CPLX, false><<<grid, kBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int TM, int TN, int U, bool CPLX>
+int occ_tsmttsm(int M, int N) {
+    const int P = ((M + TM - 1) / TM) * ((N + TN - 1) / TN);
+    if (P > kBlock) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tsmttsm<TM, TN, U, CPLX, false>, kBlock, 0) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+
+// --------------------------------------------------------------------- TSMM
+
+template <int TPR, int NPT, int U, bool CPLX>
+__global__ void __launch_bounds__(kBlock) k_tsmm(const TsmmArgs a) {
+    constexpr int CC = CPLX ? 2 : 1;
+    constexpr int RPC = kBlock / TPR;  // rows per CTA per unrolled step
+    extern __shared__ double cs[];     // alpha * C, M x N (x CC)
+    const int N = a.N, M = a.M;
+    tsmm_stage_c<CC>(a, cs);
+
+    const int r = threadIdx.x / TPR, q = threadIdx.x - r * TPR;
+    const double* __restrict__ A = a.A;
+    const int64_t sa = a.lda * CC, sb = a.ldb * CC;
+    const int64_t step = (int64_t)gridDim.x * RPC * U;
+    for (int64_t base = (int64_t)blockIdx.x * RPC * U; base < a.K; base += step) {
+        int64_t row[U];
+        bool rok[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            row[u] = base + r + (int64_t)u * RPC;
+            rok[u] = row[u] < a.K;
+            if (!rok[u]) row[u] = 0;
+        }
+        double acc[U][NPT][CC];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int j = 0; j < NPT; ++j)
+#pragma unroll
+                for (int c = 0; c < CC; ++c) acc[u][j][c] = 0.0;
+#pragma unroll 2
+        for (int m = 0; m < M; ++m) {
+            double av[U][CC];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int c = 0; c < CC; ++c) av[u][c] = rok[u] ? __ldg(A + row[u] * sa + m * CC + c) : 0.0;
+#pragma unroll
+            for (int j = 0; j < NPT; ++j) {
+                const int n = q + j * TPR;
+                if (n < N) {
+                    const double cr = cs[(m * N + n) * CC];
+                    const double ci = cs[(m * N + n) * CC + CC - 1];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        if (!CPLX) {
+                            acc[u][j][0] = fma(av[u][0], cr, acc[u][j][0]);
+                        } else {
+                            const double ar = av[u][0], ai = av[u][CC - 1];
+                            acc[u][j][0] = fma(ar, cr, acc[u][j][0]);
+                            acc[u][j][0] = fma(-ai, ci, acc[u][j][0]);
+                            acc[u][j][CC - 1] = fma(ar, ci, acc[u][j][CC - 1]);
+                            acc[u][j][CC - 1] = fma(ai, cr, acc[u][j][CC - 1]);
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!rok[u]) continue;
+            double* out = a.B + row[u] * sb;
+#pragma unroll
+            for (int j = 0; j < NPT; ++j) {
+                const int n = q + j * TPR;
+                if (n >= N) continue;
+                tsmm_store<CC>(a, out, n, acc[u][j][0], acc[u][j][CC - 1]);
+            }
+        }
+    }
+}
+
+template <int TPR, int NPT, int U, bool CPLX>
+size_t tsmm_smem(int M, int N) {
+    return (size_t)M * N * (CPLX ? 2 : 1) * sizeof(double);
+}
+
+template <int TPR, int NPT, int U, bool CPLX>
+cudaError_t launch_tsmm(const TsmmArgs& a, int grid, cudaStream_t s) {
+    const size_t smem = tsmm_smem<TPR, NPT, U, CPLX>(a.M, a.N);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_tsmm<TPR, NPT, U, CPLX>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_tsmm<TPR, NPT, U, CPLX><<<grid, kBlock, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int TPR, int NPT, int U, bool CPLX>
+int occ_tsmm(int M, int N) {
+    if (N > TPR * NPT) return 0;
+    const size_t smem = tsmm_smem<TPR, NPT, U, CPLX>(M, N);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_tsmm<TPR, NPT, U, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tsmm<TPR, NPT, U, CPLX>, kBlock, smem) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+
+// ------------------------------------------------------------ scale kernels
+
+__global__ void k_scale(double* X, int64_t rows, int cols, int64_t ld, int cplx, double br, double bi,
+                        int beta_zero) {
+    const int64_t total = rows * cols;
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < total;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = o / cols, c = o - r * cols;
+        if (!cplx) {
+            double* p = X + r * ld + c;
+            *p = beta_zero ? 0.0 : br * *p;
+        } else {
+            double* p = X + (r * ld + c) * 2;
+            if (beta_zero) {
+                p[0] = 0.0;
+                p[1] = 0.0;
+            } else {
+                const double xr = p[0], xi = p[1];
+                p[0] = br * xr - bi * xi;
+                p[1] = br * xi + bi * xr;
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------- registration
+
+template <int TM, int TN, int U, bool CPLX>
+Variant make_tsmttsm() {
+    Variant v;
+    memset(&v, 0, sizeof(v));
+    snprintf(v.info.name, sizeof(v.info.name), "tsmttsm_%s_direct_t%dx%d_u%d", CPLX ? "c64" : "r64", TM, TN,
+             U);
+    v.info.kind = TSM_KIND_TSMTTSM;
+    v.info.dtype = CPLX ? TSM_C64 : TSM_R64;
+    v.info.tile_m = TM;
+    v.info.tile_n = TN;
+    v.info.unroll = U;
+    v.info.block = kBlock;
+    v.tsmttsm = launch_tsmttsm<TM, TN, U, CPLX>;
+    v.occupancy = occ_tsmttsm<TM, TN, U, CPLX>;
+    return v;
+}
+
+template <int TPR, int NPT, int U, bool CPLX>
+Variant make_tsmm() {
+    Variant v;
+    memset(&v, 0, sizeof(v));
+    snprintf(v.info.name, sizeof(v.info.name), "tsmm_%s_smemc_tpr%d_npt%d_u%d", CPLX ? "c64" : "r64", TPR,
+             NPT, U);
+    v.info.kind = TSM_KIND_TSMM;
+    v.info.dtype = CPLX ? TSM_C64 : TSM_R64;
+    v.info.tile_n = NPT;
+    v.info.threads_per_row = TPR;
+    v.info.unroll = U;
+    v.info.block = kBlock;
+    v.tsmm = launch_tsmm<TPR, NPT, U, CPLX>;
+    v.occupancy = occ_tsmm<TPR, NPT, U, CPLX>;
+    return v;
+}
+
+template <bool CPLX>
+void add_tsmttsm(std::vector<Variant>& t) {
+    t.push_back(make_tsmttsm<1, 1, 4, CPLX>());
+    t.push_back(make_tsmttsm<2, 2, 2, CPLX>());
+    t.push_back(make_tsmttsm<2, 2, 4, CPLX>());
+    t.push_back(make_tsmttsm<4, 4, 1, CPLX>());
+    t.push_back(make_tsmttsm<4, 4, 2, CPLX>());
+    t.push_back(make_tsmttsm<8, 4, 1, CPLX>());
+    t.push_back(make_tsmttsm<4, 8, 1, CPLX>());
+    if (!CPLX) t.push_back(make_tsmttsm<8, 8, 1, CPLX>());
+}
+
+template <bool CPLX>
+void add_tsmm(std::vector<Variant>& t) {
+    t.push_back(make_tsmm<1, 1, 4, CPLX>());
+    t.push_back(make_tsmm<1, 2, 4, CPLX>());
+    t.push_back(make_tsmm<1, 4, 2, CPLX>());
+    t.push_back(make_tsmm<2, 1, 4, CPLX>());
+    t.push_back(make_tsmm<2, 2, 4, CPLX>());
+    t.push_back(make_tsmm<2, 4, 2, CPLX>());
+    t.push_back(make_tsmm<4, 1, 4, CPLX>());
+    t.push_back(make_tsmm<4, 2, 4, CPLX>());
+    t.push_back(make_tsmm<4, 4, 2, CPLX>());
+    t.push_back(make_tsmm<4, 8, 1, CPLX>());
+    t.push_back(make_tsmm<4, 16, 1, CPLX>());
+    t.push_back(make_tsmm<8, 1, 4, CPLX>());
+    t.push_back(make_tsmm<8, 2, 2, CPLX>());
+    t.push_back(make_tsmm<8, 4, 2, CPLX>());
+    t.push_back(make_tsmm<8, 8, 1, CPLX>());
+    t.push_back(make_tsmm<16, 1, 4, CPLX>());
+    t.push_back(make_tsmm<16, 2, 2, CPLX>());
+    t.push_back(make_tsmm<16, 4, 1, CPLX>());
+    t.push_back(make_tsmm<16, 4, 2, CPLX>());
+    t.push_back(make_tsmm<32, 1, 2, CPLX>());
+    t.push_back(make_tsmm<32, 2, 1, CPLX>());
+}
+
+}  // namespace
+
+void register_fp64_variants(std::vector<Variant>& tsmttsm, std::vector<Variant>& tsmm) {
+    add_tsmttsm<false>(tsmttsm);
+    add_tsmttsm<true>(tsmttsm);
+    add_tsmm<false>(tsmm);
+    add_tsmm<true>(tsmm);
+}
+
+cudaError_t launch_scale_small(double* C, int rows, int cols, int64_t ld, int cplx, double br, double bi,
+                               int beta_zero, cudaStream_t s) {
+    const int64_t total = (int64_t)rows * cols;
+    const int grid = (int)((total + 255) / 256);
+    k_scale<<<grid > 0 ? grid : 1, 256, 0, s>>>(C, rows, cols, ld, cplx, br, bi, beta_zero);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_tall(double* B, int64_t rows, int cols, int64_t ld, int cplx, double br, double bi,
+                              int beta_zero, cudaStream_t s) {
+    const int grid = device_info().sm_count * 8;
+    k_scale<<<grid, 256, 0, s>>>(B, rows, cols, ld, cplx, br, bi, beta_zero);
+    return cudaGetLastError();
+}
+
+}  // namespace tsm

@@ -1,0 +1,171 @@
+// Machine-peak probes (Sec. 1.6 of the paper: own micro-benchmarks for the
+// bandwidth and FP64 ceilings of the roofline model).
+#include "tsm_internal.h"
+#include "tsm_probe.h"
+
+namespace tsm {
+namespace {
+
+constexpr int kChains = 8;  // independent FMA chains per thread
+
+__global__ void k_dfma_peak(int64_t iters, double seed, double* out) {
+    double x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = seed + threadIdx.x * 1e-7 + c;
+    const double m = 0.999999999, a = 1e-9;
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) x[c] = fma(x[c], m, a);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += x[c];
+    if (s == 12345.678) out[0] = s;  // keeps the chains alive
+}
+
+__global__ void k_dmma_peak(int64_t iters, double seed, double* out) {
+    double acc[4][2];
+    double av = seed + threadIdx.x * 1e-9, bv = 1.0 - threadIdx.x * 1e-9;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[c][0] = acc[c][1] = 0.0;
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            asm volatile(
+                "mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};\n"
+                : "+d"(acc[c][0]), "+d"(acc[c][1])
+                : "d"(av), "d"(bv));
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) s += acc[c][0] + acc[c][1];
+    if (s == 12345.678) out[0] = s;
+}
+
+template <int ILP>
+__global__ void k_read(const double2* __restrict__ x, int64_t n, double* out) {
+    double s0 = 0.0, s1 = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + (ILP - 1) * stride < n; i += ILP * stride) {
+        double2 v[ILP];
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) v[u] = __ldcs(x + i + u * stride);
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) {
+            s0 += v[u].x;
+            s1 += v[u].y;
+        }
+    }
+    for (; i < n; i += stride) {
+        const double2 v = __ldcs(x + i);
+        s0 += v.x;
+        s1 += v.y;
+    }
+    if (s0 + s1 == 12345.678) out[0] = s0;
+}
+
+template <int ILP>
+__global__ void k_scale_stream(double2* x, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + (ILP - 1) * stride < n; i += ILP * stride) {
+        double2 v[ILP];
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) v[u] = __ldcs(x + i + u * stride);
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) __stcs(x + i + u * stride, make_double2(v[u].x * 1.0, v[u].y * 1.0));
+    }
+    for (; i < n; i += stride) __stcs(x + i, __ldcs(x + i));
+}
+
+struct Timer {
+    cudaEvent_t a, b;
+    cudaStream_t s;
+    bool ok;
+    explicit Timer(cudaStream_t st) : s(st) {
+        ok = cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess;
+    }
+    ~Timer() {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+    void start() { cudaEventRecord(a, s); }
+    float stop() {
+        cudaEventRecord(b, s);
+        float ms = 0.f;
+        if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return -1.f;
+        return ms;
+    }
+};
+
+}  // namespace
+}  // namespace tsm
+
+using namespace tsm;
+
+extern "C" tsm_status tsm_probe_fp64(int mode, int64_t iters, double* gflops, tsm_stream_t stream) {
+    if ((mode != 0 && mode != 1) || !gflops || iters < 1) return TSM_ERR_INVALID_VALUE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int sm = device_info().sm_count;
+    double* dummy = nullptr;
+    if (cudaMalloc(&dummy, 64) != cudaSuccess) return TSM_ERR_ALLOC;
+    const int blocks = sm * 4, threads = 256;
+    Timer t(s);
+    if (!t.ok) {
+        cudaFree(dummy);
+        return TSM_ERR_LAUNCH;
+    }
+    double flops = 0.0;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {  // first pass warms up clocks
+        t.start();
+        if (mode == 0)
+            k_dfma_peak<<<blocks, threads, 0, s>>>(iters, 1.0, dummy);
+        else
+            k_dmma_peak<<<blocks, threads, 0, s>>>(iters, 1.0, dummy);
+        ms = t.stop();
+    }
+    if (mode == 0)
+        flops = 2.0 * kChains * (double)iters * blocks * threads;
+    else
+        flops = 2.0 * 8 * 8 * 4 * 4 * (double)iters * blocks * (threads / 32);
+    cudaFree(dummy);
+    if (ms <= 0.f || cudaGetLastError() != cudaSuccess) return TSM_ERR_LAUNCH;
+    *gflops = flops / (ms * 1e-3) / 1e9;
+    return TSM_OK;
+}
+
+extern "C" tsm_status tsm_probe_bandwidth(void* buffer, size_t bytes, int mode, int ilp, int blocks_per_sm,
+                                          double* gbs, tsm_stream_t stream) {
+    if (!buffer || !gbs || bytes < 16 || (bytes % 16) || ((uintptr_t)buffer % 16)) return TSM_ERR_INVALID_VALUE;
+    if ((mode != 0 && mode != 1) || (ilp != 1 && ilp != 4 && ilp != 16) || blocks_per_sm < 0)
+        return TSM_ERR_INVALID_VALUE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int sm = device_info().sm_count;
+    const int bps = blocks_per_sm > 0 ? blocks_per_sm : 8;
+    const int blocks = sm * bps;
+    const int64_t n = (int64_t)(bytes / 16);
+    double* dummy = nullptr;
+    if (cudaMalloc(&dummy, 64) != cudaSuccess) return TSM_ERR_ALLOC;
+    Timer t(s);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        t.start();
+        if (mode == 0) {
+            if (ilp == 1) k_read<1><<<blocks, 256, 0, s>>>((const double2*)buffer, n, dummy);
+            if (ilp == 4) k_read<4><<<blocks, 256, 0, s>>>((const double2*)buffer, n, dummy);
+            if (ilp == 16) k_read<16><<<blocks, 256, 0, s>>>((const double2*)buffer, n, dummy);
+        } else {
+            if (ilp == 1) k_scale_stream<1><<<blocks, 256, 0, s>>>((double2*)buffer, n);
+            if (ilp == 4) k_scale_stream<4><<<blocks, 256, 0, s>>>((double2*)buffer, n);
+            if (ilp == 16) k_scale_stream<16><<<blocks, 256, 0, s>>>((double2*)buffer, n);
+        }
+        const float ms = t.stop();
+        if (ms > 0.f && ms < best) best = ms;
+    }
+    cudaFree(dummy);
+    if (best >= 1e29f || cudaGetLastError() != cudaSuccess) return TSM_ERR_LAUNCH;
+    *gbs = (double)bytes * (mode == 1 ? 2.0 : 1.0) / (best * 1e-3) / 1e9;
+    return TSM_OK;
+}

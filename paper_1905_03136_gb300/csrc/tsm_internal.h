@@ -1,0 +1,87 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "tsm.h"
+
+namespace tsm {
+
+constexpr int kBlock = 256;  // threads per CTA of the FP64 kernels
+
+// Arguments of one TSMTTSM launch (device pointers; alpha/beta by value).
+struct TsmttsmArgs {
+    int M, N;
+    int64_t K;
+    const double* A;  // K x lda (complex: interleaved pairs)
+    int64_t lda;
+    const double* B;  // K x ldb
+    int64_t ldb;
+    double* C;        // M x ldc
+    int64_t ldc;
+    double alpha_r, alpha_i, beta_r, beta_i;
+    int beta_zero;    // 1: C is not read
+    int conj;         // 1: A^H B
+    double* ws;       // grid * M * N * c partial sums
+    unsigned* ticket; // one counter, zero between launches
+};
+
+// Arguments of one TSMM launch.
+struct TsmmArgs {
+    int M, N;
+    int64_t K;
+    const double* A;  // K x lda
+    int64_t lda;
+    const double* Cm; // M x ldc
+    int64_t ldc;
+    double* B;        // K x ldb
+    int64_t ldb;
+    double alpha_r, alpha_i, beta_r, beta_i;
+    int beta_zero;
+};
+
+typedef cudaError_t (*TsmttsmLaunch)(const TsmttsmArgs&, int grid, cudaStream_t);
+typedef cudaError_t (*TsmmLaunch)(const TsmmArgs&, int grid, cudaStream_t);
+// Resident CTAs per SM for this variant and shape (0 if it cannot run).
+typedef int (*OccupancyFn)(int M, int N);
+
+struct Variant {
+    tsm_variant_info info;
+    TsmttsmLaunch tsmttsm;  // exactly one of the two launchers is set
+    TsmmLaunch tsmm;
+    OccupancyFn occupancy;
+};
+
+// Variant tables, filled once in a fixed order (indices are stable within a
+// build): hand-written families first, then code-generator output.
+void register_fp64_variants(std::vector<Variant>& tsmttsm, std::vector<Variant>& tsmm);
+void register_generated_variants(std::vector<Variant>& tsmttsm, std::vector<Variant>& tsmm);
+
+// Device properties of the current device, cached.
+struct DeviceInfo {
+    int device;
+    int sm_count;
+    int cc_major, cc_minor;
+    size_t smem_optin;
+};
+const DeviceInfo& device_info();
+
+// Per-(device, stream) scratch: partial sums + reduction tickets.
+struct Workspace {
+    double* partials;
+    size_t partial_bytes;
+    unsigned* tickets;
+    int ticket_count;
+};
+tsm_status workspace_get(cudaStream_t stream, size_t partial_bytes, int tickets, Workspace** out);
+
+// Scale-only updates (K == 0 or alpha == 0 paths).
+cudaError_t launch_scale_small(double* C, int rows, int cols, int64_t ld, int cplx, double br,
+                               double bi, int beta_zero, cudaStream_t s);
+cudaError_t launch_scale_tall(double* B, int64_t rows, int cols, int64_t ld, int cplx, double br,
+                              double bi, int beta_zero, cudaStream_t s);
+
+}  // namespace tsm

@@ -1,0 +1,139 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function
+declared in include/*.h, describes its variants consistently, and rejects
+malformed arguments before touching a device."""
+
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1905_03136_gb300 import build, _lib
+    if not os.path.exists(_lib.LIB_PATH):
+        build.build()
+    return _lib.load()
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(tsm_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_headers_declare_entry_points():
+    names = _declared_functions()
+    for required in ("tsm_tsmttsm", "tsm_tsmm", "tsm_status_string", "tsm_tune", "tsm_fill_random"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1905_03136_gb300 import _lib
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\sT\s(tsm_\w+)", out))
+    missing = _declared_functions() - exported
+    assert not missing, "declared but not exported: %s" % sorted(missing)
+
+
+def test_binding_covers_declared_functions(lib):
+    import importlib
+    import pkgutil
+    import paper_1905_03136_gb300 as pkg
+    from paper_1905_03136_gb300 import _lib
+    # sub-modules register the signatures of their headers on import
+    for m in pkgutil.iter_modules(pkg.__path__):
+        if m.name not in ("build", "codegen", "__main__", "libtsm"):
+            importlib.import_module("paper_1905_03136_gb300." + m.name)
+    missing = _declared_functions() - set(_lib.SIGNATURES)
+    assert not missing, "no Python binding for: %s" % sorted(missing)
+
+
+def test_status_strings(lib):
+    for s in range(8):
+        assert lib.tsm_status_string(s)
+    assert lib.tsm_status_string(99) == b"unknown status"
+
+
+def test_variant_table(lib):
+    import paper_1905_03136_gb300 as t
+    for kind in (t.KIND_TSMTTSM, t.KIND_TSMM):
+        vs = t.variants(kind)
+        assert len(vs) > 10
+        names = [v["name"] for v in vs]
+        assert len(set(names)) == len(names)
+        assert any(v["generated"] for v in vs) and any(not v["generated"] for v in vs)
+        for v in vs:
+            assert v["kind"] == kind and v["dtype"] in (0, 1)
+    info = t.VariantInfo()
+    assert lib.tsm_variant_get(0, 10 ** 6, ctypes.byref(info)) == 1
+    assert lib.tsm_variant_count(7) == -1
+
+
+def test_generic_variant_supports_every_shape(lib):
+    import paper_1905_03136_gb300 as t
+    for kind in (t.KIND_TSMTTSM, t.KIND_TSMM):
+        for dt in (t.R64, t.C64):
+            for M in (1, 3, 17, 64):
+                for N in (1, 5, 32, 64):
+                    ok = [i for i in range(lib.tsm_variant_count(kind))
+                          if lib.tsm_variant_supports(kind, i, dt, M, N)]
+                    assert ok, (kind, dt, M, N)
+
+
+def _call_tsmttsm(lib, op=1, dt=0, M=4, N=4, K=10, lda=4, ldb=4, ldc=4, A=1, B=1, C=1, alpha=True,
+                  beta=True):
+    from paper_1905_03136_gb300._lib import scalar
+    return lib.tsm_tsmttsm(op, dt, M, N, K, scalar(1.0, 1) if alpha else None, ctypes.c_void_p(A),
+                           lda, ctypes.c_void_p(B), ldb, scalar(0.0, 1) if beta else None,
+                           ctypes.c_void_p(C), ldc, None)
+
+
+def test_argument_validation_without_device(lib):
+    INVALID, UNSUPPORTED = 1, 2
+    assert _call_tsmttsm(lib, M=0) == UNSUPPORTED
+    assert _call_tsmttsm(lib, N=65) == UNSUPPORTED
+    assert _call_tsmttsm(lib, K=-1) == INVALID
+    assert _call_tsmttsm(lib, op=0) == INVALID
+    assert _call_tsmttsm(lib, op=7) == INVALID
+    assert _call_tsmttsm(lib, dt=5) == INVALID
+    assert _call_tsmttsm(lib, lda=3) == INVALID
+    assert _call_tsmttsm(lib, ldb=2) == INVALID
+    assert _call_tsmttsm(lib, ldc=3) == INVALID
+    assert _call_tsmttsm(lib, C=0) == INVALID
+    assert _call_tsmttsm(lib, A=0) == INVALID
+    assert _call_tsmttsm(lib, alpha=False) == INVALID
+    assert _call_tsmttsm(lib, beta=False) == INVALID
+    from paper_1905_03136_gb300._lib import scalar
+    # TSMM: only op N; transposed C is a valid request this library does not implement
+    one, zero = scalar(1.0, 0), scalar(0.0, 0)
+    assert lib.tsm_tsmm(1, 0, 4, 4, 10, one, ctypes.c_void_p(1), 4, ctypes.c_void_p(1), 4, zero,
+                        ctypes.c_void_p(1), 4, None) == UNSUPPORTED
+    assert lib.tsm_tsmm(9, 0, 4, 4, 10, one, ctypes.c_void_p(1), 4, ctypes.c_void_p(1), 4, zero,
+                        ctypes.c_void_p(1), 4, None) == INVALID
+    assert lib.tsm_tsmm(0, 0, 4, 4, 10, one, ctypes.c_void_p(1), 3, ctypes.c_void_p(1), 4, zero,
+                        ctypes.c_void_p(1), 4, None) == INVALID
+    assert lib.tsm_tsmm(0, 0, 4, 4, 10, one, ctypes.c_void_p(1), 4, ctypes.c_void_p(1), 4, zero,
+                        ctypes.c_void_p(0), 4, None) == INVALID
+    assert lib.tsm_fill_random(ctypes.c_void_p(1), 0, 4, 4, 0, 0, 9, None) == INVALID
+
+
+def test_no_device_is_an_error_not_a_fallback(lib):
+    """Without a GPU a well-formed call must fail (NO_DEVICE), never compute
+    on the host."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    assert _call_tsmttsm(lib) == 7

@@ -1,0 +1,217 @@
+"""Parity of the FP64 CUDA kernels against the CPU oracle (GPU required).
+
+Every compiled variant that supports a shape is run through the C ABI on the
+same seeded inputs as the oracle and compared element by element:
+normwise relative Frobenius error <= 1e-12 for random data (the bound the
+method must meet), bit-exact for small-integer data (every partial sum is
+an exact integer, so any summation order gives the same bits).
+"""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def tsm():
+    import paper_1905_03136_gb300 as t
+    from paper_1905_03136_gb300 import build, _lib
+    import os
+    if not os.path.exists(_lib.LIB_PATH):
+        build.build()
+    t.load()
+    return t
+
+
+def dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _variants_for(tsm, kind, dt, M, N):
+    lib = tsm.load()
+    return [i for i in range(lib.tsm_variant_count(kind)) if lib.tsm_variant_supports(kind, i, dt, M, N)]
+
+
+TSMTTSM_SHAPES = [(1, 1), (2, 2), (2, 3), (4, 4), (7, 5), (8, 8), (16, 16), (33, 17), (32, 32), (64, 64),
+                  (1, 64), (64, 1), (8, 32), (32, 8), (13, 64)]
+TSMM_SHAPES = [(1, 1), (2, 2), (3, 5), (4, 4), (8, 8), (16, 16), (31, 7), (32, 32), (64, 64), (4, 64),
+               (64, 4), (1, 64), (64, 1)]
+
+
+@pytest.mark.parametrize("cplx", [False, True], ids=["r64", "c64"])
+@pytest.mark.parametrize("shape", TSMTTSM_SHAPES, ids=lambda s: "%dx%d" % s)
+def test_tsmttsm_every_variant(tsm, shape, cplx):
+    M, N = shape
+    K = 4097
+    A = synth.block_vector(0, K, M, complex_=cplx)
+    B = synth.block_vector(1, K, N, complex_=cplx)
+    dA, dB = dev(A), dev(B)
+    dt = tsm.C64 if cplx else tsm.R64
+    ops = ("T", "C") if cplx else ("T",)
+    vs = _variants_for(tsm, tsm.KIND_TSMTTSM, dt, M, N)
+    assert vs
+    for op in ops:
+        ref = oracle.gram(A, B, op)
+        for v in vs:
+            for grid in (0, 7):
+                C = tsm.tsmttsm(dA, dB, op=op, variant=v, grid=grid)
+                err = oracle.rel_fro(host(C), ref)
+                assert err <= TOL, (tsm.variants(tsm.KIND_TSMTTSM)[v]["name"], op, grid, err)
+
+
+@pytest.mark.parametrize("cplx", [False, True], ids=["r64", "c64"])
+@pytest.mark.parametrize("shape", [(1, 1), (3, 5), (16, 16), (64, 64), (64, 1)], ids=lambda s: "%dx%d" % s)
+def test_tsmttsm_integer_inputs_bitwise(tsm, shape, cplx):
+    M, N = shape
+    K = 3001
+    A = synth.block_vector(5, K, M, complex_=cplx, dist="smallint")
+    B = synth.block_vector(6, K, N, complex_=cplx, dist="smallint")
+    dA, dB = dev(A), dev(B)
+    dt = tsm.C64 if cplx else tsm.R64
+    for op in (("T", "C") if cplx else ("T",)):
+        ref = oracle.gram(A, B, op)
+        for v in _variants_for(tsm, tsm.KIND_TSMTTSM, dt, M, N):
+            C = host(tsm.tsmttsm(dA, dB, op=op, variant=v))
+            assert np.array_equal(C, ref), tsm.variants(tsm.KIND_TSMTTSM)[v]["name"]
+
+
+@pytest.mark.parametrize("cplx", [False, True], ids=["r64", "c64"])
+def test_tsmttsm_alpha_beta_ld_and_nan(tsm, cplx):
+    import torch
+    M, N, K = 6, 5, 20011
+    lda, ldb, ldc = M + 3, N + 1, N + 2
+    A = synth.block_vector(11, K, M, ld=lda, complex_=cplx)
+    B = synth.block_vector(12, K, N, ld=ldb, complex_=cplx, dist="loguniform")
+    C0 = synth.block_vector(13, M, N, ld=ldc, complex_=cplx)
+    alpha, beta = (0.5 - 1.25j, 2.0 + 0.5j) if cplx else (0.5, -2.0)
+    ref = C0.copy()
+    oracle.tsmttsm("C" if cplx else "T", M, N, K, alpha, A, lda, B, ldb, beta, ref, ldc)
+    dA, dB = dev(A), dev(B)
+    dC = dev(C0)
+    tsm.tsmttsm(dA[:, :M], dB[:, :N], dC[:, :N], alpha, beta, op="C" if cplx else "T")
+    got = host(dC)
+    assert oracle.rel_fro(got[:, :N], ref[:, :N]) <= TOL
+    assert np.array_equal(got[:, N:], C0[:, N:]), "padding columns of C were written"
+    # beta = 0: NaNs in C must not propagate
+    nanC = dev(np.full((M, ldc), np.nan, dtype=C0.dtype))
+    tsm.tsmttsm(dA[:, :M], dB[:, :N], nanC[:, :N], alpha, 0.0, op="C" if cplx else "T")
+    ref0 = np.zeros((M, N), dtype=C0.dtype)
+    oracle.tsmttsm("C" if cplx else "T", M, N, K, alpha, A, lda, B, ldb, 0.0, ref0, N)
+    assert oracle.rel_fro(host(nanC)[:, :N], ref0) <= TOL
+    # K = 0 and alpha = 0: C = beta * C exactly
+    dC2 = dev(C0)
+    tsm.tsmttsm(dA[:0, :M], dB[:0, :N], dC2[:, :N], alpha, beta, op="T")
+    exp = C0.copy()
+    exp[:, :N] = beta * C0[:, :N]
+    assert np.allclose(host(dC2), exp, rtol=1e-15, atol=0)
+    dC3 = dev(C0)
+    tsm.tsmttsm(dA[:, :M], dB[:, :N], dC3[:, :N], 0.0, beta, op="T")
+    assert np.allclose(host(dC3), exp, rtol=1e-15, atol=0)
+    del torch
+
+
+def test_tsmttsm_small_k_and_determinism(tsm):
+    import torch
+    for K in (1, 2, 3, 5, 151, 1217):
+        A = synth.block_vector(21, K, 8)
+        B = synth.block_vector(22, K, 3)
+        C = host(tsm.tsmttsm(dev(A), dev(B)))
+        assert oracle.rel_fro(C, oracle.gram(A, B)) <= TOL, K
+    A = dev(synth.block_vector(23, 300007, 16, complex_=True))
+    B = dev(synth.block_vector(24, 300007, 16, complex_=True))
+    c1 = host(tsm.tsmttsm(A, B, op="C"))
+    for _ in range(3):
+        assert np.array_equal(host(tsm.tsmttsm(A, B, op="C")), c1)
+    del torch
+
+
+@pytest.mark.parametrize("cplx", [False, True], ids=["r64", "c64"])
+@pytest.mark.parametrize("shape", TSMM_SHAPES, ids=lambda s: "%dx%d" % s)
+def test_tsmm_every_variant(tsm, shape, cplx):
+    M, N = shape
+    K = 5003
+    A = synth.block_vector(31, K, M, complex_=cplx)
+    Cm = synth.small_matrix(32, M, N, complex_=cplx)
+    B0 = synth.block_vector(33, K, N, complex_=cplx)
+    dA, dC = dev(A), dev(Cm)
+    dt = tsm.C64 if cplx else tsm.R64
+    alpha, beta = (1.5 + 0.5j, -0.5 + 1j) if cplx else (1.5, -0.5)
+    ref0 = oracle.apply(A, Cm)
+    ref1 = oracle.apply(A, Cm, alpha, beta, B0)
+    vs = _variants_for(tsm, tsm.KIND_TSMM, dt, M, N)
+    assert vs
+    for v in vs:
+        for grid in (0, 5):
+            B = tsm.tsmm(dA, dC, variant=v, grid=grid)
+            err = oracle.rel_fro(host(B), ref0)
+            assert err <= TOL, (tsm.variants(tsm.KIND_TSMM)[v]["name"], grid, err)
+        dB = dev(B0)
+        tsm.tsmm(dA, dC, dB, alpha, beta, variant=v)
+        err = oracle.rel_fro(host(dB), ref1)
+        assert err <= TOL, (tsm.variants(tsm.KIND_TSMM)[v]["name"], "alpha/beta", err)
+
+
+@pytest.mark.parametrize("cplx", [False, True], ids=["r64", "c64"])
+def test_tsmm_integer_bitwise_identity_and_ld(tsm, cplx):
+    M, N, K = 12, 9, 4099
+    A = synth.block_vector(41, K, M, complex_=cplx, dist="smallint")
+    Cm = synth.small_matrix(42, M, N, complex_=cplx, dist="smallint")
+    dt = tsm.C64 if cplx else tsm.R64
+    ref = oracle.apply(A, Cm)
+    dA, dC = dev(A), dev(Cm)
+    for v in _variants_for(tsm, tsm.KIND_TSMM, dt, M, N):
+        assert np.array_equal(host(tsm.tsmm(dA, dC, variant=v)), ref)
+    # C = I reproduces A bit for bit
+    I = np.eye(M, dtype=A.dtype)
+    assert np.array_equal(host(tsm.tsmm(dev(synth.block_vector(43, K, M, complex_=cplx)), dev(I))),
+                          synth.block_vector(43, K, M, complex_=cplx))
+    # padded leading dimensions; padding of B untouched; NaN B with beta = 0
+    lda, ldc, ldb = M + 5, N + 3, N + 4
+    A2 = synth.block_vector(44, K, M, ld=lda, complex_=cplx)
+    C2 = synth.block_vector(45, M, N, ld=ldc, complex_=cplx)
+    B2 = np.full((K, ldb), np.nan, dtype=A2.dtype)
+    dB2 = dev(B2)
+    tsm.tsmm(dev(A2)[:, :M], dev(C2)[:, :N], dB2[:, :N], 1.0, 0.0)
+    got = host(dB2)
+    ref2 = np.zeros((K, N), dtype=A2.dtype)
+    oracle.tsmm(M, N, K, 1.0, A2, lda, C2, ldc, 0.0, ref2, N)
+    assert oracle.rel_fro(got[:, :N], ref2) <= TOL
+    assert np.all(np.isnan(got[:, N:]))
+
+
+def test_device_fill_matches_host_generator(tsm):
+    import torch
+    for dist in ("uniform", "loguniform", "smallint", "ones"):
+        for cplx in (False, True):
+            rows, ld, row0 = 1031, 7, 12345
+            t = torch.empty((rows, ld), dtype=torch.complex128 if cplx else torch.float64, device="cuda")
+            tsm.fill_random(t, seed=9, dist=dist, row0=row0)
+            ref = synth.block_vector(9, rows, ld, complex_=cplx, dist=dist, row0=row0)
+            assert np.array_equal(host(t), ref), (dist, cplx)
+
+
+def test_gram_schmidt_step_on_device(tsm):
+    """B' = B - Q (Q^H B) with both products on the GPU leaves Q^H B' ~ 0."""
+    K, M, N = 200003, 8, 6
+    X = synth.block_vector(51, K, M, complex_=True)
+    Q = np.ascontiguousarray(np.linalg.qr(X)[0])
+    B = synth.block_vector(52, K, N, complex_=True)
+    dQ, dB = dev(Q), dev(B)
+    C = tsm.tsmttsm(dQ, dB, op="C")
+    tsm.tsmm(dQ, C, dB, -1.0, 1.0)
+    R = host(tsm.tsmttsm(dQ, dB, op="C"))
+    assert np.abs(R).max() < 1e-12 * np.linalg.norm(B)
