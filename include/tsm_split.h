@@ -1,0 +1,66 @@
+/*
+ * tsm_split.h -- split-precision TSMTTSM on the tensor cores.
+ *
+ * The paper computes both products in binary64 on the FP64 units.  On GB300
+ * the FP64 rate is about 1.25 TFLOP/s, so TSMTTSM is FP64-bound for every
+ * width above one.  This entry point computes the same product,
+ *     C = alpha * op(A)^T B + beta * C            (op = T, or C for A^H)
+ * with error-free splitting in the style of Ozaki, Ogita, Oishi and Rump
+ * ("Error-free transformations of matrix multiplication by using fast
+ * routines of matrix multiplication and its applications", Numer. Algorithms
+ * 59, 2012): every input column is scaled by a power of two and cut into six
+ * signed 8-bit integer slices held exactly in bfloat16, the slice products
+ * run on the tensor cores (tcgen05, FP32 accumulation in tensor memory kept
+ * exact by bounding the rows per accumulation tile), and the slice products
+ * are recombined and reduced over K in binary64.  Complex data is handled
+ * as the real product of the interleaved (re, im) columns.
+ *
+ * Accuracy: each input keeps 47 bits below its column's running maximum and
+ * slice products with combined weight below 2^-54 are dropped, so
+ * |C_split - C_exact| is a few units of 2^-47 relative to sum |a||b| per
+ * entry; the normwise relative error against the FP64 oracle is about
+ * 1e-13 on uniform and log-uniform inputs.  Inputs must be finite (NaN/Inf
+ * are not propagated; use tsm_tsmttsm for them).  Results are
+ * deterministic for a fixed problem and device.
+ *
+ * Arguments, layout, ownership and argument errors as tsm_tsmttsm (tsm.h);
+ * any alignment and leading dimension is accepted.  Work is asynchronous on
+ * `stream` (two kernels: the split product and a fixed-order reduction of
+ * the per-CTA partials); the library's per-(device, stream) workspace holds
+ * the partial sums and an error word that tsm_split_status() reads.
+ */
+#ifndef TSM_SPLIT_H
+#define TSM_SPLIT_H
+
+#include "tsm.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+tsm_status tsm_tsmttsm_split(tsm_op opA, tsm_dtype dtype, int M, int N,
+                             int64_t K, const double *alpha, const void *A,
+                             int64_t lda, const void *B, int64_t ldb,
+                             const double *beta, void *C, int64_t ldc,
+                             tsm_stream_t stream);
+
+/*
+ * Synchronizes `stream` and reports whether the most recent
+ * tsm_tsmttsm_split on it hit a bounded device-side wait that gave up
+ * (TSM_ERR_TIMEOUT; that call's C then holds NaN) -- TSM_OK otherwise.
+ * Clears the word.
+ */
+tsm_status tsm_split_status(tsm_stream_t stream);
+
+/*
+ * Test hook: the same kernel with every device-side wait limited to
+ * `timeout_cycles` SM clock cycles (<= 0 restores the default of about
+ * two seconds).  Affects later calls on all streams.
+ */
+tsm_status tsm_split_set_timeout(int64_t timeout_cycles);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSM_SPLIT_H */

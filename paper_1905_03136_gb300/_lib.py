@@ -11,6 +11,7 @@ import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtsm.so")
+DEFAULT_TABLE = os.path.join(_HERE, "tuning", "gb300_sm103.txt")
 
 TSM_OK = 0
 STATUS_NAMES = {0: "TSM_OK", 1: "TSM_ERR_INVALID_VALUE", 2: "TSM_ERR_NOT_SUPPORTED", 3: "TSM_ERR_ALLOC",
@@ -93,6 +94,10 @@ def load():
                 fn = getattr(lib, name)
                 fn.restype = res
                 fn.argtypes = args
+            # The autotuned table for this GPU ships with the package; an
+            # explicit TSM_TUNE_FILE replaces it.
+            if not os.environ.get("TSM_TUNE_FILE") and os.path.exists(DEFAULT_TABLE):
+                lib.tsm_load_tuning(DEFAULT_TABLE.encode())
             _lib = lib
     return _lib
 

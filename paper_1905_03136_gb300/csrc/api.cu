@@ -150,12 +150,31 @@ static int heuristic_variant(tsm_kind kind, int dtype, int M, int N) {
     char name[64];
     const char* dt = dtype == TSM_C64 ? "c64" : "r64";
     if (kind == TSM_KIND_TSMTTSM) {
-        if (M * N == 1)
-            snprintf(name, sizeof(name), "tsmttsm_%s_direct_t1x1_u4", dt);
-        else if (M <= 8 && N <= 8)
-            snprintf(name, sizeof(name), "tsmttsm_%s_direct_t2x2_u2", dt);
-        else
-            snprintf(name, sizeof(name), "tsmttsm_%s_direct_t4x4_u1", dt);
+        // Hand-written tiles only: least padding waste (FMAs on guarded,
+        // out-of-range tile entries), then the larger tile (fewer loads per
+        // FMA, Sec. 3), then fewer rows unrolled.
+        int best = -1;
+        double best_waste = 1e30;
+        int best_area = 0, best_u = 0;
+        for (size_t i = 0; i < t.size(); ++i) {
+            const tsm_variant_info& f = t[i].info;
+            if (f.generated || !variant_supports(t[i], dtype, M, N)) continue;
+            const int pm = (M + f.tile_m - 1) / f.tile_m, pn = (N + f.tile_n - 1) / f.tile_n;
+            const double waste = (double)(pm * f.tile_m) * (pn * f.tile_n) / ((double)M * N);
+            const int area = f.tile_m * f.tile_n;
+            if (area * (dtype == TSM_C64 ? 2 : 1) > 16) continue;
+            const bool better = waste < best_waste - 1e-9 ||
+                                (waste < best_waste + 1e-9 && (area > best_area ||
+                                                               (area == best_area && f.unroll > best_u)));
+            if (better) {
+                best = (int)i;
+                best_waste = waste;
+                best_area = area;
+                best_u = f.unroll;
+            }
+        }
+        if (best >= 0) return best;
+        snprintf(name, sizeof(name), "tsmttsm_%s_direct_t1x1_u4", dt);
     } else {
         int tpr = N >= 16 ? 16 : (N >= 8 ? 8 : (N >= 4 ? 4 : (N >= 2 ? 2 : 1)));
         int npt = (N + tpr - 1) / tpr;

@@ -5,19 +5,48 @@
 
 namespace tsm {
 
+// Sum of the G per-CTA partials of entry o (CC doubles each) over the CTA
+// slice s, s + S, s + 2S, ... in that fixed order; 8 loads in flight.
+template <int CC>
+__device__ __forceinline__ void sum_partials(const double* ws, int MNc, int o, int G, int s, int S,
+                                             double* out) {
+    double acc[CC][8];
+#pragma unroll
+    for (int c = 0; c < CC; ++c)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) acc[c][r] = 0.0;
+    int b = s;
+    for (; b + 7 * S < G; b += 8 * S)
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < CC; ++c) acc[c][r] += __ldcg(ws + (int64_t)(b + r * S) * MNc + o * CC + c);
+    for (; b < G; b += S)
+#pragma unroll
+        for (int c = 0; c < CC; ++c) acc[c][0] += __ldcg(ws + (int64_t)b * MNc + o * CC + c);
+#pragma unroll
+    for (int c = 0; c < CC; ++c)
+        out[c] = ((acc[c][0] + acc[c][1]) + (acc[c][2] + acc[c][3])) +
+                 ((acc[c][4] + acc[c][5]) + (acc[c][6] + acc[c][7]));
+}
+
 // Deterministic two-level reduction of TSMTTSM partial tiles (replaces the
 // atomics of Sec. 3.2).  Thread (lane, p) holds acc[(i * TN + j) * CC + c] for
 // C[pm + i*PM][pn + j*PN] with pm = p % PM, pn = p / PM.
-//   1. lanes are summed through shared memory in lane order, one tile entry
-//      at a time, into this CTA's M x N partial in the workspace;
-//   2. the last CTA to take the ticket sums all partials in CTA order (four
-//      interleaved accumulators, combined pairwise), applies
-//      alpha * sum + beta * C (C not read when beta == 0) and resets the
-//      ticket for the next launch.
+//   1. the L lanes of each tile entry are summed through shared memory by a
+//      pairwise tree with a fixed pairing (lane l absorbs lane l + h), one
+//      tile entry at a time, into this CTA's M x N partial in the workspace;
+//   2. the last CTA to take the ticket sums all partials: S threads share
+//      each entry, thread s taking CTAs s, s + S, ... in order, and the S
+//      slice sums are added in slice order; then alpha * sum + beta * C (C
+//      not read when beta == 0) is stored and the ticket reset for the next
+//      launch.
+// Every order above depends only on (G, M, N, tile), so results repeat bit
+// for bit.
 template <int TM, int TN, int CC>
 __device__ __forceinline__ void tsmttsm_finish(const TsmttsmArgs& a, const double* acc, int PM, int PN,
                                                int L, int lane, int p, bool active) {
-    __shared__ double red[kBlock];
+    __shared__ double red[kBlock * CC];
     __shared__ unsigned s_last;
     const int M = a.M, N = a.N;
     const int P = PM * PN;
@@ -32,13 +61,15 @@ __device__ __forceinline__ void tsmttsm_finish(const TsmttsmArgs& a, const doubl
             for (int c = 0; c < CC; ++c) {
                 if (active) red[lane * P + p] = acc[(i * TN + j) * CC + c];
                 __syncthreads();
+                for (int n = L; n > 1;) {
+                    const int h = (n + 1) >> 1;
+                    if (active && lane + h < n) red[lane * P + p] += red[(lane + h) * P + p];
+                    __syncthreads();
+                    n = h;
+                }
                 if (t < P) {
                     const int m = (t % PM) + i * PM, n = (t / PM) + j * PN;
-                    if (m < M && n < N) {
-                        double s = 0.0;
-                        for (int l = 0; l < L; ++l) s += red[l * P + t];
-                        part[(m * N + n) * CC + c] = s;
-                    }
+                    if (m < M && n < N) part[(m * N + n) * CC + c] = red[t];
                 }
                 __syncthreads();
             }
@@ -51,24 +82,27 @@ __device__ __forceinline__ void tsmttsm_finish(const TsmttsmArgs& a, const doubl
     __threadfence();
     const int MN = M * N;
     const int G = gridDim.x;
-    for (int o = t; o < MN; o += blockDim.x) {
-        double s[CC][4];
-#pragma unroll
-        for (int c = 0; c < CC; ++c)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) s[c][r] = 0.0;
-        int b = 0;
-        for (; b + 3 < G; b += 4)
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int c = 0; c < CC; ++c) s[c][r] += __ldcg(a.ws + (int64_t)(b + r) * MNc + o * CC + c);
-        for (; b < G; ++b)
-#pragma unroll
-            for (int c = 0; c < CC; ++c) s[c][0] += __ldcg(a.ws + (int64_t)b * MNc + o * CC + c);
+    // S threads per entry when there are fewer entries than threads.
+    int S = 1;
+    while (S * 2 * MN <= (int)blockDim.x && S * 2 <= G) S *= 2;
+    for (int base = 0; base < MN * S; base += blockDim.x) {
+        const int w = base + t;
         double v[CC];
+        const bool mine = w < MN * S;
+        if (mine) sum_partials<CC>(a.ws, MNc, w / S, G, w % S, S, v);
+        if (S > 1) {
+            // slice sums of one entry are adjacent threads: combine in order
 #pragma unroll
-        for (int c = 0; c < CC; ++c) v[c] = (s[c][0] + s[c][1]) + (s[c][2] + s[c][3]);
+            for (int c = 0; c < CC; ++c) red[t * CC + c] = mine ? v[c] : 0.0;
+            __syncthreads();
+            if (mine && (w % S) == 0)
+                for (int s = 1; s < S; ++s)
+#pragma unroll
+                    for (int c = 0; c < CC; ++c) v[c] += red[(t + s) * CC + c];
+            __syncthreads();
+        }
+        if (!mine || (w % S) != 0) continue;
+        const int o = w / S;
         const int m = o / N, n = o - m * N;
         double* out = a.C + ((int64_t)m * a.ldc + n) * CC;
         if (CC == 1) {

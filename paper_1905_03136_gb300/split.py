@@ -1,0 +1,44 @@
+"""Binding of the split-precision TSMTTSM (include/tsm_split.h)."""
+
+import ctypes
+
+from . import _lib
+from ._lib import scalar
+
+_lib.extend_signatures({
+    "tsm_tsmttsm_split": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_int64,
+                                         ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "tsm_split_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "tsm_split_set_timeout": (ctypes.c_int, [ctypes.c_int64]),
+})
+
+_OPS = {"T": 1, "C": 2}
+
+
+def tsmttsm_split(A, B, C=None, alpha=1.0, beta=0.0, op="T", stream=None):
+    """C = alpha * op(A)^T B + beta * C with the tensor-core split path."""
+    import torch
+    from . import _dtype_code, _ld, _stream
+    dt = _dtype_code(A)
+    K, M = A.shape
+    N = B.shape[1]
+    if C is None:
+        C = torch.zeros((M, N), dtype=A.dtype, device=A.device)
+        beta = 0.0
+    cplx = dt == 1
+    _lib.call("tsm_tsmttsm_split", _OPS[op], dt, M, N, K, scalar(alpha, cplx), ctypes.c_void_p(A.data_ptr()),
+              _ld(A, "A"), ctypes.c_void_p(B.data_ptr()), _ld(B, "B"), scalar(beta, cplx),
+              ctypes.c_void_p(C.data_ptr()), _ld(C, "C"), _stream(stream))
+    return C
+
+
+def status(stream=None):
+    """Raw status of the last split call on the stream (0 OK, 5 timeout)."""
+    from . import _stream
+    return _lib.raw("tsm_split_status")(_stream(stream))
+
+
+def set_timeout(cycles):
+    _lib.call("tsm_split_set_timeout", int(cycles))
