@@ -51,6 +51,12 @@ tsm_status tsm_time_variant(tsm_kind kind, tsm_dtype dtype, int M, int N,
                             int variant, int grid, int reps, float *ms,
                             tsm_stream_t stream);
 
+/* Grid sizes tsm_tune tries for a variant and shape: writes up to `max`
+ * values to `grids` and their count to *count (0 if the variant cannot run
+ * the shape).  Needs the device (occupancy query). */
+tsm_status tsm_tune_grids(tsm_kind kind, int variant, tsm_dtype dtype, int M,
+                          int N, int *grids, int max, int *count);
+
 /* Puts one entry into the tuning table (e.g. a model's prediction). */
 tsm_status tsm_set_tuning(tsm_kind kind, tsm_dtype dtype, int M, int N,
                           int64_t K, int variant, int grid);

@@ -64,6 +64,7 @@ SIGNATURES = {
     "tsm_time_variant": (i32, [i32, i32, i32, i32, i64, vp, i64, vp, i64, vp, i64, i32, i32, i32,
                                ctypes.POINTER(ctypes.c_float), vp]),
     "tsm_set_tuning": (i32, [i32, i32, i32, i32, i64, i32, i32]),
+    "tsm_tune_grids": (i32, [i32, i32, i32, i32, i32, ctypes.POINTER(i32), i32, ctypes.POINTER(i32)]),
     "tsm_load_tuning": (i32, [ctypes.c_char_p]),
     "tsm_save_tuning": (i32, [ctypes.c_char_p]),
     "tsm_clear_tuning": (i32, []),

@@ -87,11 +87,16 @@ def main():
     ap.add_argument("--table", default=DEFAULT_TABLE)
     ap.add_argument("--log", default=None, help="append measurements (JSON lines) here")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--random", type=int, default=0,
+                    help="tune this many random (dtype, M, N) shapes instead of the sweep")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--keep-table", action="store_true", help="merge into the loaded table")
     args = ap.parse_args()
     import torch
     import paper_1905_03136_gb300 as tsm
     lib = tsm.load()
-    lib.tsm_clear_tuning()
+    if not args.keep_table:
+        lib.tsm_clear_tuning()
     log = open(args.log, "a") if args.log else None
     K = args.K
     flatA = torch.empty(K * 128, dtype=torch.float64, device="cuda")
@@ -99,8 +104,15 @@ def main():
     tsm.fill_random(flatA.view(K, 128), 0)
     tsm.fill_random(flatB.view(K, 128), 1)
     kinds = {"tsmttsm": [0], "tsmm": [1], "both": [0, 1]}[args.kind]
+    import numpy as np
+    rng = np.random.default_rng(args.seed)
     for kind in kinds:
-        tune_shapes(kind, sweep_shapes(kind), K, args.reps, log, (flatA, flatB))
+        if args.random:
+            shapes = [(bool(rng.integers(0, 2)), int(rng.integers(1, 65)), int(rng.integers(1, 65)))
+                      for _ in range(args.random)]
+        else:
+            shapes = sweep_shapes(kind)
+        tune_shapes(kind, shapes, K, args.reps, log, (flatA, flatB))
     os.makedirs(os.path.dirname(os.path.abspath(args.table)), exist_ok=True)
     tsm._lib.call("tsm_save_tuning", args.table.encode())
     print("table written to", args.table)

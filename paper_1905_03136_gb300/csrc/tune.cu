@@ -145,6 +145,29 @@ tsm_status tsm_set_tuning(tsm_kind kind, tsm_dtype dtype, int M, int N, int64_t 
     return TSM_OK;
 }
 
+tsm_status tsm_tune_grids(tsm_kind kind, int variant, tsm_dtype dtype, int M, int N, int* grids, int max,
+                          int* count) {
+    if (!grids || !count || max < 0) return TSM_ERR_INVALID_VALUE;
+    *count = 0;
+    if (!supports(kind, variant, dtype, M, N)) return TSM_OK;
+    const Variant* var = variant_at(kind, variant);
+    const int occ = var->occupancy ? var->occupancy(M, N) : 1;
+    if (occ <= 0) return TSM_OK;
+    const int sm = device_info().sm_count;
+    // one CTA per SM, two, full occupancy, two waves
+    const int cand[4] = {sm, sm * 2, sm * occ, sm * occ * 2};
+    int n = 0;
+    for (int i = 0; i < 4; ++i) {
+        if (i < 2 && cand[i] > sm * occ) continue;
+        bool dup = false;
+        for (int j = 0; j < n; ++j) dup |= grids[j] == cand[i];
+        if (dup || n >= max) continue;
+        grids[n++] = cand[i];
+    }
+    *count = n;
+    return TSM_OK;
+}
+
 tsm_status tsm_time_variant(tsm_kind kind, tsm_dtype dtype, int M, int N, int64_t K, const void* X,
                             int64_t ldx, const void* Y, int64_t ldy, void* Z, int64_t ldz, int variant,
                             int grid, int reps, float* ms, tsm_stream_t stream) {
@@ -191,15 +214,10 @@ tsm_status tsm_tune(tsm_kind kind, tsm_dtype dtype, int M, int N, int64_t K, con
     int best_v = -1, best_g = 0;
     for (int v = 0; v < nv; ++v) {
         if (!supports(kind, v, dtype, M, N)) continue;
-        const Variant* var = variant_at(kind, v);
-        const int occ = var->occupancy ? var->occupancy(M, N) : 1;
-        if (occ <= 0) continue;
-        int grids[4] = {sm, sm * 2, sm * occ, sm * occ * 2};
-        for (int gi = 0; gi < 4; ++gi) {
+        int grids[4], ng = 0;
+        if (tsm_tune_grids(kind, v, dtype, M, N, grids, 4, &ng) != TSM_OK) continue;
+        for (int gi = 0; gi < ng; ++gi) {
             const int g = grids[gi];
-            bool dup = false;
-            for (int j = 0; j < gi; ++j) dup |= grids[j] == g;
-            if (dup || (gi < 2 && grids[gi] > sm * occ)) continue;
             float ms = 0.f;
             tsm_status st = tsm_time_variant(kind, dtype, M, N, K, X, ldx, Y, ldy, Z, ldz, v, g, reps, &ms, stream);
             if (st != TSM_OK) return st;

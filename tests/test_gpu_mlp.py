@@ -1,0 +1,101 @@
+"""The cost model's network kernels against the float64 oracle: forward
+values, gradient of the mean squared error, one Adam step, reproducible
+training; and the learned tuner's regret against exhaustive search."""
+
+import os
+
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    import paper_1905_03136_gb300 as t
+    from paper_1905_03136_gb300 import build, _lib, mlp
+    if not os.path.exists(_lib.LIB_PATH):
+        build.build()
+    t.load()
+    return mlp
+
+
+def _case(D=17, H=64, n=300, seed=3):
+    rng = np.random.default_rng(seed)
+    p = rng.uniform(-0.3, 0.3, omlp.param_count(D, H)).astype(np.float32)
+    X = rng.uniform(-1, 1, (n, D)).astype(np.float32)
+    t = rng.uniform(-1, 1, n).astype(np.float32)
+    return p, X, t
+
+
+def test_forward_and_gradient_match_oracle(M):
+    import torch
+    D, H = 17, 64
+    p, X, t = _case(D, H)
+    net = M.Mlp(D, H, max_batch=1024)
+    net.set_params(p)
+    dX, dt = torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda()
+    y = net.forward(dX).cpu().numpy()
+    y_ref = omlp.forward(p, X, D, H)
+    assert np.max(np.abs(y - y_ref)) <= 1e-5 * max(1.0, np.max(np.abs(y_ref)))
+    loss = float(net.backward(dX, dt).item())
+    assert abs(loss - omlp.loss(p, X, t, D, H)) <= 1e-5 * max(1.0, loss)
+    g = net.grads().astype(np.float64)
+    g_ref = omlp.grad(p, X, t, D, H)
+    assert np.max(np.abs(g - g_ref)) <= 1e-4 * np.max(np.abs(g_ref))
+    # the oracle's gradient itself against central differences in float64
+    i = int(np.argmax(np.abs(g_ref)))
+    e = np.zeros_like(g_ref)
+    e[i] = 1e-6
+    fd = (omlp.loss(p.astype(np.float64) + e, X, t, D, H) - omlp.loss(p.astype(np.float64) - e, X, t, D, H)) / 2e-6
+    assert abs(fd - g_ref[i]) <= 1e-6 * abs(g_ref[i]) + 1e-12
+
+
+def test_adam_step_matches_oracle(M):
+    import torch
+    D, H = 5, 8
+    p, X, t = _case(D, H, n=50)
+    net = M.Mlp(D, H, max_batch=64)
+    net.set_params(p)
+    net.backward(torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda())
+    g = net.grads().astype(np.float64)
+    net.adam(lr=1e-2)
+    torch.cuda.synchronize()
+    p_ref, _, _ = omlp.adam(p.astype(np.float64), g, 0.0, 0.0, 1, 1e-2)
+    assert np.max(np.abs(net.params() - p_ref)) <= 1e-6
+
+
+def test_training_is_reproducible_and_learns(M):
+    import torch
+    rng = np.random.default_rng(5)
+    X = rng.uniform(-1, 1, (2000, 6)).astype(np.float32)
+    t = (np.sin(2 * X[:, 0]) + X[:, 1] * X[:, 2]).astype(np.float32)
+    dX, dt = torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda()
+    a = M.Mlp(6, 64, max_batch=4096, seed=11)
+    b = M.Mlp(6, 64, max_batch=4096, seed=11)
+    ha = a.fit(dX, dt, epochs=600, lr=3e-3)
+    hb = b.fit(dX, dt, epochs=600, lr=3e-3)
+    assert np.array_equal(a.params(), b.params())
+    assert ha[-1] < 0.1 * ha[0]
+
+
+def test_learned_tuner_regret_on_held_out_shapes(M):
+    """Trained (by the GPU kernels) on the autotuner's timing log minus
+    held-out shapes; for each held-out shape the logged time of the model's
+    pick over the logged exhaustive best must stay within 5% (geometric
+    mean), and beat the built-in heuristic's pick in total."""
+    from paper_1905_03136_gb300 import costmodel as cm
+    log = os.path.join(os.path.dirname(cm.__file__), "tuning", "timing_log.jsonl")
+    if not os.path.exists(log):
+        pytest.skip("no timing log committed yet")
+    recs = cm.load_log(log)
+    shapes = sorted({cm.shape_key(r) for r in recs})
+    held = [s for i, s in enumerate(shapes) if i % 5 == 2]
+    train = [r for r in recs if cm.shape_key(r) not in set(held)]
+    model = cm.CostModel(seed=1)
+    model.fit(train, epochs=3000)
+    reg = cm.regret_from_log(model, recs, held)
+    geo = float(np.exp(np.mean(np.log(list(reg.values())))))
+    assert geo <= 1.05, (geo, sorted(reg.values())[-5:])
