@@ -1,0 +1,107 @@
+// TSMTTSM without device allocations: the per-CTA partial sums and the
+// reduction ticket of the deterministic two-level reduction live in one
+// fixed array compiled into the library, instead of the per-stream
+// workspace that tsm_tsmttsm() grows with cudaMalloc.  For callers that must
+// not allocate (memory arenas that own the device, paths that cannot afford
+// the device synchronization a cudaMalloc implies).
+#include <mutex>
+
+#include "tsm_internal.h"
+#include "tsm_noalloc.h"
+#include "tune.h"
+
+// Scratch of the allocation-free entry point (held by every GPU that loads
+// the library, until exit).  In host code this name is only a handle: its
+// device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[TSM_NOALLOC_SCRATCH_BYTES];
+
+namespace tsm {
+
+tsm_status validate_common(int dtype, int M, int N, int64_t K, const double* alpha, const double* beta);
+tsm_status choose(tsm_kind kind, int dtype, int M, int N, int64_t K, int* variant, int* grid);
+
+namespace {
+
+std::mutex g_mu;
+void* g_scratch_dev[64] = {nullptr};
+
+// Device address of the scratch array on the current device; looked up once
+// per device with that device current.
+tsm_status scratch_address(void** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return TSM_ERR_NO_DEVICE;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_scratch_dev[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return TSM_ERR_LAUNCH;
+        g_scratch_dev[dev] = p;
+    }
+    *out = g_scratch_dev[dev];
+    return TSM_OK;
+}
+
+}  // namespace
+}  // namespace tsm
+
+using namespace tsm;
+
+extern "C" tsm_status tsm_tsmttsm_noalloc(tsm_op opA, tsm_dtype dtype, int M, int N, int64_t K,
+                                          const double* alpha, const void* A, int64_t lda, const void* B,
+                                          int64_t ldb, const double* beta, void* C, int64_t ldc,
+                                          tsm_stream_t stream) {
+    tsm_status st = validate_common(dtype, M, N, K, alpha, beta);
+    if (st != TSM_OK) return st;
+    if (opA != TSM_OP_T && opA != TSM_OP_C) return TSM_ERR_INVALID_VALUE;
+    if (lda < M || ldb < N || ldc < N || !C) return TSM_ERR_INVALID_VALUE;
+    const int cplx = dtype == TSM_C64;
+    const bool alpha0 = alpha[0] == 0.0 && (!cplx || alpha[1] == 0.0);
+    if (K > 0 && !alpha0 && (!A || !B)) return TSM_ERR_INVALID_VALUE;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TSM_ERR_NO_DEVICE;
+    const DeviceInfo& di = device_info();
+    if (di.cc_major != 10 || di.cc_minor != 3) return TSM_ERR_NO_DEVICE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int beta_zero = beta[0] == 0.0 && (!cplx || beta[1] == 0.0);
+    if (K == 0 || alpha0)
+        return launch_scale_small((double*)C, M, N, ldc, cplx, beta[0], cplx ? beta[1] : 0.0, beta_zero, s) ==
+                       cudaSuccess
+                   ? TSM_OK
+                   : TSM_ERR_LAUNCH;
+
+    // One CTA per SM; its partial sums must fit the array (the last 256
+    // bytes hold the ticket).
+    const int grid = di.sm_count;
+    const size_t need = (size_t)grid * M * N * (cplx ? 2 : 1) * sizeof(double);
+    if (need > (size_t)TSM_NOALLOC_SCRATCH_BYTES - 256) return TSM_ERR_NOT_SUPPORTED;
+
+    int variant = -1, unused_grid = 0;
+    if ((st = choose(TSM_KIND_TSMTTSM, dtype, M, N, K, &variant, &unused_grid)) != TSM_OK) return st;
+    const Variant* var = variant_at(TSM_KIND_TSMTTSM, variant);
+    if (!var || !var->tsmttsm) return TSM_ERR_INTERNAL;
+
+    void* scratch = nullptr;
+    if ((st = scratch_address(&scratch)) != TSM_OK) return st;
+    unsigned* ticket = reinterpret_cast<unsigned*>(static_cast<unsigned char*>(scratch) +
+                                                   TSM_NOALLOC_SCRATCH_BYTES - 256);
+    if (cudaMemsetAsync(ticket, 0, sizeof(unsigned), s) != cudaSuccess) return TSM_ERR_LAUNCH;
+
+    TsmttsmArgs a;
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.A = (const double*)A;
+    a.lda = lda;
+    a.B = (const double*)B;
+    a.ldb = ldb;
+    a.C = (double*)C;
+    a.ldc = ldc;
+    a.alpha_r = alpha[0];
+    a.alpha_i = cplx ? alpha[1] : 0.0;
+    a.beta_r = beta[0];
+    a.beta_i = cplx ? beta[1] : 0.0;
+    a.beta_zero = beta_zero;
+    a.conj = (cplx && opA == TSM_OP_C) ? 1 : 0;
+    a.ws = static_cast<double*>(scratch);
+    a.ticket = ticket;
+    return var->tsmttsm(a, grid, s) == cudaSuccess ? TSM_OK : TSM_ERR_LAUNCH;
+}
