@@ -21,6 +21,7 @@ import argparse
 import ctypes
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -129,15 +130,16 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ helpers
 
-def _kernel_source_hash():
+def _kernel_source_hash(variant_name):
+    """Hash of the sources that define a variant's kernel: the hand-written
+    FP64 family or the generator, plus their shared epilogue and header."""
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1905_03136_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(f.read())
-    with open(os.path.join(ROOT, "paper_1905_03136_gb300", "codegen.py"), "rb") as f:
-        h.update(f.read())
+    pkg = os.path.join(ROOT, "paper_1905_03136_gb300")
+    files = ["csrc/fp64_common.cuh", "csrc/tsm_internal.h"]
+    files.append("codegen.py" if variant_name.startswith("gen_") else "csrc/kernels_fp64.cu")
+    for name in files:
+        with open(os.path.join(pkg, name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -151,7 +153,7 @@ def _traffic_for(variant_name, cfg_key):
     except Exception:
         return None
     e = d.get(cfg_key)
-    if not e or e.get("source_hash") != _kernel_source_hash() or e.get("variant") != variant_name:
+    if not e or e.get("source_hash") != _kernel_source_hash(variant_name) or e.get("variant") != variant_name:
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -362,6 +364,10 @@ def run_ours(args, bw, bw_src):
                "sample": "first %d of 2^24 rows of each of the 22 sweep configurations (%.1f s of CPU), "
                          "times scaled x%d" % (args.cpu_rows, wall, K // args.cpu_rows)}
 
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras = run_extras(args, flatA, flatB, K, bw, p64)
+
     if rank == 0:
         line = {"metric": "TSMTTSM % of roofline vs width, K=2^24", "value": value, "unit": "% of roofline",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -376,6 +382,7 @@ def run_ours(args, bw, bw_src):
                           "fp64_source": p64_src, "fp64_nominal_gflops": FP64_NOMINAL_GFLOPS,
                           "dfma_probe_gflops": dfma, "dmma_probe_gflops": dmma},
                 "sweep": sweep}
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -383,8 +390,11 @@ def run_ours(args, bw, bw_src):
 
 
 def run_e2e(args, flatA, flatB, outs, views, ideal, dev, K):
-    """One sweep where every call first copies its A and B from pinned host
-    memory and reads C back: the same metric measured end to end."""
+    """One sweep where every call's A and B come from pinned host memory and
+    its C goes back to the host: the same metric measured end to end.  Each
+    configuration's inputs are copied in full (no reuse across calls); the
+    copy of the next configuration overlaps the current kernel through a
+    second stream and two device slots."""
     import torch
     try:
         hA = torch.empty(flatA.numel(), dtype=torch.float64, pin_memory=True)
@@ -396,33 +406,244 @@ def run_e2e(args, flatA, flatB, outs, views, ideal, dev, K):
         pinned = False
     hA.copy_(flatA)
     hB.copy_(flatB)
-    dA = torch.empty_like(flatA)
-    dB = torch.empty_like(flatB)
+    slots = [(torch.empty_like(flatA), torch.empty_like(flatB)) for _ in range(2)]
     hC = {cfg: torch.empty(outs[cfg].shape, dtype=outs[cfg].dtype, pin_memory=pinned) for cfg in SWEEP}
     import paper_1905_03136_gb300 as tsm
+    compute = torch.cuda.current_stream()
+    copier = torch.cuda.Stream()
     h2d = d2h = 0
+    copied = [torch.cuda.Event() for _ in SWEEP]
+    done = [torch.cuda.Event() for _ in SWEEP]
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    t0.record()
-    for cfg in SWEEP:
+    t0.record(compute)
+    copier.wait_event(t0)
+    for i, cfg in enumerate(SWEEP):
         cplx, M, N = cfg
         c = 2 if cplx else 1
         na, nb = K * M * c, K * N * c
-        dA[:na].copy_(hA[:na], non_blocking=True)
-        dB[:nb].copy_(hB[:nb], non_blocking=True)
+        dA, dB = slots[i % 2]
+        with torch.cuda.stream(copier):
+            if i >= 2:
+                copier.wait_event(done[i - 2])
+            dA[:na].copy_(hA[:na], non_blocking=True)
+            dB[:nb].copy_(hB[:nb], non_blocking=True)
+            copied[i].record(copier)
+        compute.wait_event(copied[i])
         A, B = _views(dA, dB, cplx, M, N, K)
         tsm.tsmttsm(A, B, outs[cfg], op="C" if cplx else "T")
         hC[cfg].copy_(outs[cfg], non_blocking=True)
+        done[i].record(compute)
         h2d += 8 * (na + nb)
         d2h += outs[cfg].numel() * outs[cfg].element_size()
-    t1.record()
+    t1.record(compute)
     torch.cuda.synchronize()
     secs = t0.elapsed_time(t1) * 1e-3
-    del dA, dB, hA, hB
+    # raw pinned host-to-device bandwidth of one large copy, for context
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(compute)
+    slots[0][0].copy_(hA, non_blocking=True)
+    e1.record(compute)
+    torch.cuda.synchronize()
+    h2d_gbs = 8.0 * hA.numel() / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del slots, hA, hB
     torch.cuda.empty_cache()
     return {"value": 100.0 * sum(ideal.values()) / secs, "unit": "% of roofline", "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "ms_per_step": secs * 1e3, "pinned": pinned}
+            "d2h_bytes_per_step": d2h, "ms_per_step": secs * 1e3, "pinned": pinned,
+            "h2d_gbs_single_copy": round(h2d_gbs, 1),
+            "note": "every call copies its own A and B (no reuse); copies overlap the previous kernel"}
+
+
+# ------------------------------------------------------------------ extras
+
+def _time(fn, reps=3, warm=1):
+    import torch
+    for _ in range(warm):
+        fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+SPLIT_CASES = [(True, 32, 32), (True, 48, 48), (True, 64, 64), (False, 64, 64)]
+TSMM_SWEEP = [(c, m, n) for c in (False, True) for (m, n) in [(w, w) for w in SQUARE] + [(4, 64), (64, 4)]]
+
+
+def run_split_extra(flatA, flatB, K, bw):
+    """Split-precision TSMTTSM on the split workload: time, speed-up over the
+    plain FP64 path, HBM fraction, and its normwise difference from the FP64
+    path's result (both on the GPU; the oracle pins both in the tests)."""
+    import torch
+    import paper_1905_03136_gb300 as tsm
+    from paper_1905_03136_gb300 import split
+    out = []
+    for dist in ("uniform", "loguniform"):
+        tsm.fill_random(flatA.view(K, 128), 0, dist)
+        tsm.fill_random(flatB.view(K, 128), 1, dist)
+        for (cplx, M, N) in SPLIT_CASES:
+            A, B = _views(flatA, flatB, cplx, M, N, K)
+            op = "C" if cplx else "T"
+            C1 = torch.zeros((M, N), dtype=A.dtype, device=A.device)
+            C2 = torch.zeros_like(C1)
+            ms_s = _time(lambda: split.tsmttsm_split(A, B, C1, op=op))
+            status = split.status()
+            ms_d = _time(lambda: tsm.tsmttsm(A, B, C2, op=op), reps=1)
+            rel = float(torch.linalg.norm(C1 - C2) / torch.linalg.norm(C2))
+            c = 2 if cplx else 1
+            nbytes = 8.0 * c * (M + N) * K
+            out.append({"dist": dist, "dtype": "c64" if cplx else "r64", "M": M, "N": N,
+                        "ms_split": round(ms_s, 3), "ms_fp64": round(ms_d, 3), "speedup": round(ms_d / ms_s, 2),
+                        "split_gbs": round(nbytes / (ms_s * 1e-3) / 1e9, 1),
+                        "hbm_frac": round(nbytes / (ms_s * 1e-3) / 1e9 / bw, 3),
+                        "rel_diff_vs_fp64_path": rel, "status": status})
+    tsm.fill_random(flatA.view(K, 128), 0)
+    tsm.fill_random(flatB.view(K, 128), 1)
+    return out
+
+
+def run_tsmm_extra(flatA, flatB, K, bw, p64):
+    import torch
+    import paper_1905_03136_gb300 as tsm
+    out, ideal, meas = [], 0.0, 0.0
+    Bout = torch.empty(K * 128, dtype=torch.float64, device=flatA.device)
+    for (cplx, M, N) in TSMM_SWEEP:
+        c = 2 if cplx else 1
+        A = flatA[: K * M * c]
+        Cm = flatB[: M * N * c]
+        Bo = Bout[: K * N * c]
+        if cplx:
+            A, Cm, Bo = A.view(torch.complex128), Cm.view(torch.complex128), Bo.view(torch.complex128)
+        A, Cm, Bo = A.view(K, M), Cm.view(M, N), Bo.view(K, N)
+        ms = _time(lambda: tsm.tsmm(A, Cm, Bo), reps=1)
+        flops, nbytes = model(cplx, M, N, K)
+        t_ideal = max(nbytes / (bw * 1e9), flops / (p64 * 1e9))
+        ideal += t_ideal
+        meas += ms * 1e-3
+        out.append({"dtype": "c64" if cplx else "r64", "M": M, "N": N, "ms": round(ms, 4),
+                    "roofline_pct": round(100 * t_ideal / (ms * 1e-3), 2)})
+    del Bout
+    torch.cuda.empty_cache()
+    return {"roofline_pct_whole_sweep": 100 * ideal / meas, "calls": out}
+
+
+def batched_workload(seed=0, count=256):
+    """The batched mixed workload: op TSMTTSM/TSMM and dtype 50/50, M, N
+    uniform in [1, 64], K = floor(2^(16 + 6u)) (log-uniform in [2^16, 2^22])."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        out.append((int(rng.integers(0, 2)), bool(rng.integers(0, 2)), int(rng.integers(1, 65)),
+                    int(rng.integers(1, 65)), int(2 ** (16 + 6 * rng.random()))))
+    return out
+
+
+def batched_configs_from_model(insts, model):
+    """Per-instance configuration picked by the cost model among the batched
+    kernel's codes (tile codes for TSMTTSM, threads-per-row codes for TSMM)."""
+    import numpy as np
+    from paper_1905_03136_gb300 import costmodel as cm
+    tiles = {1: (1, 1, 4), 2: (2, 2, 2), 3: (4, 4, 1), 4: (4, 8, 1), 5: (8, 4, 1)}
+    tprs = {1: 4, 2: 8, 3: 16}
+    cfg = []
+    for (kind, cplx, M, N, K) in insts:
+        cands, feats = [], []
+        if kind == 0:
+            for code, (tm, tn, u) in tiles.items():
+                if math.ceil(M / tm) * math.ceil(N / tn) > 256:
+                    continue
+                cands.append(code)
+                feats.append(cm.featurize(0, int(cplx), M, N, K, tm, tn, 1, u, 0, 0, 152))
+        else:
+            for code, tpr in tprs.items():
+                cands.append(code)
+                feats.append(cm.featurize(1, int(cplx), M, N, K, 1, math.ceil(N / tpr), tpr, 2, 0, 0, 152))
+        pred = model.predict_log2_ineff(feats)
+        cfg.append(cands[int(np.argmin(pred))])
+    return cfg
+
+
+def run_batched_extra(flatA, flatB):
+    """256 instances in one graph launch: default configurations vs the cost
+    model's, against launching every instance separately."""
+    import torch
+    from paper_1905_03136_gb300 import batched as bt
+    from paper_1905_03136_gb300 import costmodel as cm
+    import paper_1905_03136_gb300 as tsm
+    insts = batched_workload()
+    dev = flatA.device
+    outs, views = [], []
+    for (kind, cplx, M, N, K) in insts:
+        c = 2 if cplx else 1
+        dt = torch.complex128 if cplx else torch.float64
+        A = flatA[: K * M * c]
+        if kind == 0:
+            B = flatB[: K * N * c]
+            O = torch.zeros(M * N * c, dtype=torch.float64, device=dev)
+        else:
+            B = flatB[: M * N * c]
+            O = torch.zeros(K * N * c, dtype=torch.float64, device=dev)
+        if cplx:
+            A, B, O = A.view(dt), B.view(dt), O.view(dt)
+        A = A.view(K, M)
+        B = B.view(K, N) if kind == 0 else B.view(M, N)
+        O = O.view(M, N) if kind == 0 else O.view(K, N)
+        views.append((A, B, O))
+    flops = sum(2.0 * M * N * K * (4 if c else 1) for (_, c, M, N, K) in insts)
+    res = {"instances": len(insts), "flops": flops}
+
+    def make(cfgs):
+        descs = [bt.desc(k, A, B, O, 1.0, 0.0, ("C" if c else "T") if k == 0 else "N", cfg)
+                 for (k, c, M, N, K), (A, B, O), cfg in zip(insts, views, cfgs)]
+        return bt.Batch(descs)
+
+    default = make([0] * len(insts))
+    res["items"], res["ctas"] = default.info()
+    res["default_graph_ms"] = _time(default.run, reps=2)
+    res["default_direct_ms"] = _time(default.run_direct, reps=1)
+    default.close()
+    model_path = os.path.join(ROOT, "paper_1905_03136_gb300", "tuning", "costmodel.npz")
+    if os.path.exists(model_path):
+        model = cm.CostModel()
+        model.load(model_path)
+        b = make(batched_configs_from_model(insts, model))
+        res["mlp_graph_ms"] = _time(b.run, reps=2)
+        b.close()
+
+    def separate():
+        for (k, c, M, N, K), (A, B, O) in zip(insts, views):
+            if k == 0:
+                tsm.tsmttsm(A, B, O, op="C" if c else "T")
+            else:
+                tsm.tsmm(A, B, O)
+    res["separate_launches_ms"] = _time(separate, reps=1)
+    res["gflops_default_graph"] = flops / (res["default_graph_ms"] * 1e-3) / 1e9
+    del views, outs
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_extras(args, flatA, flatB, K, bw, p64):
+    ex = {}
+    try:
+        ex["split"] = run_split_extra(flatA, flatB, K, bw)
+    except Exception as e:  # reported, never hidden
+        ex["split"] = {"error": repr(e)}
+    try:
+        ex["tsmm_sweep"] = run_tsmm_extra(flatA, flatB, K, bw, p64)
+    except Exception as e:
+        ex["tsmm_sweep"] = {"error": repr(e)}
+    try:
+        ex["batched"] = run_batched_extra(flatA, flatB)
+    except Exception as e:
+        ex["batched"] = {"error": repr(e)}
+    return ex
 
 
 def main():
@@ -435,6 +656,7 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=1 << 14, help="rows per config per reference-arm step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the split / TSMM / batched extras")
     ap.add_argument("--case", default=None, help="profile one config, e.g. c64:64x64")
     ap.add_argument("--k", type=int, default=1 << 20, help="rows for --case")
     ap.add_argument("--split", action="store_true", help="--case: use the split-precision path")

@@ -156,3 +156,90 @@ def regret_from_log(model, records, shapes):
         best = min(r["ms"] for r in rs)
         out[key] = pick["ms"] / best
     return out
+
+
+def heuristic_pick(kind, cplx, M, N, K):
+    """(variant name, grid) the library picks WITHOUT a tuning table or model
+    (its built-in rule); the table is restored afterwards."""
+    import os
+    import tempfile
+    import paper_1905_03136_gb300 as tsm
+    from . import _lib
+    lib = tsm.load()
+    fd, path = tempfile.mkstemp(suffix=".txt")
+    os.close(fd)
+    try:
+        _lib.call("tsm_save_tuning", path.encode())
+        lib.tsm_clear_tuning()
+        v, g = tsm.choose(kind, int(cplx), M, N, K)
+        name = tsm.variants(kind)[v]["name"]
+        _lib.call("tsm_load_tuning", path.encode())
+    finally:
+        os.unlink(path)
+    return name, g
+
+
+def evaluate(model, records, held):
+    """Held-out shapes: logged time of the model's pick, of the heuristic's
+    pick and of the exhaustive best.  Returns a summary dict."""
+    by_shape = {}
+    for r in records:
+        by_shape.setdefault(shape_key(r), []).append(r)
+    rows = []
+    for key in held:
+        rs = by_shape[key]
+        pred = model.predict_log2_ineff([record_features(r) for r in rs])
+        pick = rs[int(np.argmin(pred))]
+        best = min(r["ms"] for r in rs)
+        kind, cplx, M, N, K = key
+        hname, hgrid = heuristic_pick(kind, cplx, M, N, K)
+        hrec = [r for r in rs if r["variant"] == hname and r["grid"] == hgrid]
+        hms = hrec[0]["ms"] if hrec else float("nan")
+        rows.append({"shape": list(key), "best_ms": best, "mlp_ms": pick["ms"], "heuristic_ms": hms,
+                     "mlp_regret": pick["ms"] / best, "heuristic_regret": hms / best})
+    mr = np.array([r["mlp_regret"] for r in rows])
+    hr = np.array([r["heuristic_regret"] for r in rows])
+    ok = ~np.isnan(hr)
+    return {"held_out_shapes": len(rows), "mlp_regret_geomean": float(np.exp(np.mean(np.log(mr)))),
+            "mlp_regret_max": float(mr.max()),
+            "heuristic_regret_geomean": float(np.exp(np.mean(np.log(hr[ok])))) if ok.any() else None,
+            "mlp_total_ms": float(sum(r["mlp_ms"] for r in rows)),
+            "heuristic_total_ms": float(np.nansum([r["heuristic_ms"] for r in rows])),
+            "best_total_ms": float(sum(r["best_ms"] for r in rows)), "rows": rows}
+
+
+def main():
+    import argparse
+    import os
+    import sys
+    ap = argparse.ArgumentParser(description="train the cost model on autotuner timing logs")
+    ap.add_argument("logs", nargs="+")
+    ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning",
+                                                  "costmodel.npz"))
+    ap.add_argument("--epochs", type=int, default=3000)
+    ap.add_argument("--holdout", type=int, default=5, help="every n-th shape is held out (0: none)")
+    args = ap.parse_args()
+    recs = load_log(args.logs)
+    shapes = sorted({shape_key(r) for r in recs})
+    held = [s for i, s in enumerate(shapes) if args.holdout and i % args.holdout == 2]
+    train = [r for r in recs if shape_key(r) not in set(held)]
+    model = CostModel(seed=1)
+    hist = model.fit(train, epochs=args.epochs)
+    print("records %d shapes %d train %d held %d loss %.4f -> %.4f" % (len(recs), len(shapes), len(train),
+                                                                      len(held), hist[0], hist[-1]))
+    if held:
+        ev = evaluate(model, recs, held)
+        print(json.dumps({k: v for k, v in ev.items() if k != "rows"}))
+    # the shipped model is trained on every shape
+    full = CostModel(seed=1)
+    full.fit(recs, epochs=args.epochs)
+    full.save(args.out)
+    print("saved", args.out)
+    sys.stdout.flush()
+
+
+if __name__ == "__main__":
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    main()

@@ -23,15 +23,17 @@
 //
 // CTA organisation (one CTA per SM, persistent over a contiguous K range and
 // a chunk of Y's columns):
-//   warps 0-7  converters: load the next 16-row step of X and Y straight
-//              from global memory one step ahead (the loads of step s+1 are in
-//              flight while step s is converted: the paper's leap frogging,
-//              Sec. 3.1), update the running column exponents, and write the
-//              six bf16 slices into shared memory in the canonical K-major
-//              core-matrix layout of the MMA operands;
-//   warp 8     allocates tensor memory and issues tcgen05.mma (one thread);
-//   warps 9-12 epilogue: drain tensor memory after each tile (tcgen05.ld),
-//              recombine, accumulate in binary64 in shared memory.
+//   warps 0-15  converters: stage upcoming 16-row steps of X and Y from
+//               global memory into a per-thread cp.async ring several steps
+//               ahead (loads of later steps are in flight while step s is
+//               converted: the paper's leap frogging, Sec. 3.1, made deep),
+//               update the running column exponents, and write the six bf16
+//               slices into shared memory in the canonical K-major
+//               core-matrix layout of the MMA operands; one unit of work is
+//               4 rows of one column;
+//   warp 16     allocates tensor memory and issues tcgen05.mma (one thread);
+//   warps 17-20 epilogue: drain tensor memory after each tile (tcgen05.ld),
+//               recombine, accumulate in binary64 in shared memory.
 // MMA operand A (M = 128 rows): X slices, two slices per 128-row block when
 // P <= 64 ("stacked"), one slice per block when 64 < P <= 128.  Operand B
 // (N rows): the six Y slices stacked, Qp rows each.  Accumulator column
@@ -53,14 +55,15 @@ namespace split {
 constexpr int KSTEP = 16;           // rows per MMA (bf16: K = 16)
 constexpr int TILE_STEPS = 16;      // steps per exact accumulation tile (256 rows)
 constexpr int NSLICE = 6;           // 8-bit slices per input
-constexpr int NDIG = 3;             // digit stages (converters -> MMA)
+constexpr int NDIG = 2;             // digit stages (converters -> MMA)
+constexpr int NST_MAX = 8;          // FP64 staging stages (cp.async ring, per thread)
 constexpr int NEXP = 4;             // exponent snapshot ring (converters -> epilogue)
-constexpr int NCONV_WARPS = 8;
+constexpr int NCONV_WARPS = 16;
 constexpr int NCONV = NCONV_WARPS * 32;
-constexpr int MMA_WARP = 8;
-constexpr int EPI_WARP0 = 9;
+constexpr int MMA_WARP = 16;
+constexpr int EPI_WARP0 = 17;
 constexpr int NEPI_WARPS = 4;
-constexpr int NTHREADS = (EPI_WARP0 + NEPI_WARPS) * 32;  // 416
+constexpr int NTHREADS = (EPI_WARP0 + NEPI_WARPS) * 32;  // 672
 constexpr int TMEM_COLS = 512;
 constexpr int E_NONE = -4000;       // running exponent before any nonzero value
 constexpr long long kDefaultTimeout = 4000000000ll;  // SM cycles (~2 s)
@@ -108,13 +111,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
                                           int code) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
+    unsigned ns = 16;  // back off so waiting warps leave issue slots to working ones
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
         if (clock64() - t0 > timeout) {
             atomicCAS(err, 0, code);
             return false;
         }
-        __nanosleep(32);
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
     }
 }
 __device__ __forceinline__ void fence_proxy_async() {
@@ -169,6 +174,8 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 
 struct Layout {
     int nrb;            // 128-row blocks of operand A per step
+    int units;          // (column, 4-row group) units per step: 4 * (P + Qw)
+    int nst;            // FP64 staging stages
     uint32_t a_bytes;   // operand A bytes per step
     uint32_t b_bytes;   // operand B bytes per step
     uint32_t stage;     // digit stage bytes (1024-aligned)
@@ -176,12 +183,17 @@ struct Layout {
     uint32_t acc_off;   // binary64 accumulators [Qp][128]
     uint32_t exp_off;   // running exponents [P + Qp] then snapshots [NEXP][P + Qp]
     uint32_t misc_off;  // barriers, flags, tmem slot
+    uint32_t stg_off;   // FP64 staging ring: nst x [4 rows][units] doubles
+    uint32_t stg_bytes; // bytes per staging stage
     uint32_t total;
 };
 
-__host__ __device__ inline Layout make_layout(int P, int Qp, int stacked) {
+constexpr uint32_t kSmemBudget = 227u * 1024u;
+
+__host__ __device__ inline Layout make_layout(int P, int Qp, int Qw, int stacked) {
     Layout L;
     L.nrb = stacked ? 3 : 6;
+    L.units = 4 * (P + Qw);
     L.a_bytes = (uint32_t)L.nrb * 4096u;
     L.b_bytes = (uint32_t)NSLICE * Qp * 32u;
     L.stage = ((L.a_bytes + L.b_bytes) + 1023u) & ~1023u;
@@ -190,9 +202,39 @@ __host__ __device__ inline Layout make_layout(int P, int Qp, int stacked) {
     const uint32_t ne = (uint32_t)(P + Qp);
     L.exp_off = L.acc_off + (uint32_t)Qp * 128u * 8u;
     L.misc_off = (L.exp_off + (1u + NEXP) * ne * 4u + 127u) & ~127u;
-    L.total = L.misc_off + 512u;
+    L.stg_off = (L.misc_off + 512u + 127u) & ~127u;
+    L.stg_bytes = (uint32_t)L.units * 32u;
+    // as many staging stages as fit (at least 2), up to NST_MAX
+    int nst = 2;
+    const int opts[4] = {8, 6, 4, 3};
+    for (int i = 0; i < 4; ++i)
+        if (L.stg_off + (uint32_t)opts[i] * L.stg_bytes <= kSmemBudget) {
+            nst = opts[i];
+            break;
+        }
+    L.nst = nst;
+    L.total = L.stg_off + (uint32_t)nst * L.stg_bytes;
     if (L.total < 120u * 1024u) L.total = 120u * 1024u;  // one CTA per SM (tensor memory is taken whole)
     return L;
+}
+
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(valid ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Waits until at most `pending` of this thread's groups are in flight.
+__device__ __forceinline__ void cp_async_wait(int pending) {
+    switch (pending) {
+        case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
+        case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+        case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+        case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+        case 4: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
+        case 5: asm volatile("cp.async.wait_group 5;" ::: "memory"); break;
+        case 6: asm volatile("cp.async.wait_group 6;" ::: "memory"); break;
+        default: asm volatile("cp.async.wait_group 7;" ::: "memory"); break;
+    }
 }
 
 // misc area: byte offsets of the barriers and flags
@@ -213,33 +255,39 @@ enum {
 
 // ------------------------------------------------------------ digit maths
 
-// Six balanced base-256 digits of |x| scaled to 47 fractional bits under
-// 2^e, each as a float (exact), most significant first.  Requires |x| < 2^e
-// (or x == 0).  Returns true if x is negative.
-__device__ __forceinline__ bool split6(double x, int e, float* f) {
+// Six balanced base-256 digits of |x| truncated to 47 fractional bits under
+// 2^e, each as a float (exact), most significant first: |x| 2^(47-e) ~ X =
+// sum_s d_s 2^(40-8s), d_0 in [0, 128], d_1..d_5 in [-128, 127].  Requires
+// |x| < 2^e.  Subnormals are handled exactly (no implicit bit).  Returns the
+// sign bit of x.
+//   X: the 53-bit significand shifted right by e + 1028 - max(ef, 1) >= 6
+//      (clamped to 63, which leaves 0 for values below the column's range);
+//   balanced digits: add 0x80 to each of the five low bytes (with carries),
+//      read the bytes back and remove the bias -- one PRMT places a byte into
+//      the float 2^23 + byte, one FADD removes 2^23 (+ 128).
+__device__ __forceinline__ uint32_t split6(double x, int e, float* f) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
     const uint32_t hi = (uint32_t)(bits >> 32);
     const int ef = (int)((hi >> 20) & 0x7FFu);
-    const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (ef ? (1ull << 52) : 0ull);
-    const int sh = e + 1028 - (ef > 0 ? ef : 1);
-    unsigned long long X = 0;
-    if (mant != 0 && sh < 64) X = (mant + (1ull << (sh - 1))) >> sh;
+    const uint32_t mhi = (hi & 0xFFFFFu) | (ef ? 0x100000u : 0u);
+    const unsigned long long mant = ((unsigned long long)mhi << 32) | (uint32_t)bits;
+    const int sh = min(e + 1028 - max(ef, 1), 63);
+    const unsigned long long X = mant >> sh;
     const unsigned long long Yb = X + 0x8080808080ull;
-    const uint32_t lo = (uint32_t)Yb, hi8 = (uint32_t)(Yb >> 32);
-    f[0] = __uint_as_float(0x4B000000u | (hi8 >> 8)) - 8388608.0f;             // top digit, 0..128
-    f[1] = __uint_as_float(0x4B000000u | (hi8 & 0xFFu)) - 8388736.0f;          // byte 4 - 128
-    f[2] = __uint_as_float(0x4B000000u | (lo >> 24)) - 8388736.0f;             // byte 3 - 128
-    f[3] = __uint_as_float(0x4B000000u | ((lo >> 16) & 0xFFu)) - 8388736.0f;   // byte 2 - 128
-    f[4] = __uint_as_float(0x4B000000u | ((lo >> 8) & 0xFFu)) - 8388736.0f;    // byte 1 - 128
-    f[5] = __uint_as_float(0x4B000000u | (lo & 0xFFu)) - 8388736.0f;           // byte 0 - 128
-    return (hi >> 31) != 0;
+    const uint32_t lo = (uint32_t)Yb, h8 = (uint32_t)(Yb >> 32);
+    f[0] = __uint_as_float(__byte_perm(h8, 0x4B000000u, 0x7541)) - 8388608.0f;   // top digit
+    f[1] = __uint_as_float(__byte_perm(h8, 0x4B000000u, 0x7540)) - 8388736.0f;   // byte 4 - 128
+    f[2] = __uint_as_float(__byte_perm(lo, 0x4B000000u, 0x7543)) - 8388736.0f;   // byte 3 - 128
+    f[3] = __uint_as_float(__byte_perm(lo, 0x4B000000u, 0x7542)) - 8388736.0f;   // byte 2 - 128
+    f[4] = __uint_as_float(__byte_perm(lo, 0x4B000000u, 0x7541)) - 8388736.0f;   // byte 1 - 128
+    f[5] = __uint_as_float(__byte_perm(lo, 0x4B000000u, 0x7540)) - 8388736.0f;   // byte 0 - 128
+    return hi & 0x80000000u;
 }
 
-// Bounding exponent of one value: |x| < 2^e (E_NONE for zero).
-__device__ __forceinline__ int exp_of(double x) {
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-    if ((bits << 1) == 0) return E_NONE;
-    const int ef = (int)((bits >> 52) & 0x7FFu);
+// Exponent from the largest magnitude high word of a column: |x| < 2^e for
+// every x of the column (zero and subnormal columns give the subnormal bound).
+__device__ __forceinline__ int exp_from_hi(uint32_t hmax) {
+    const int ef = (int)(hmax >> 20);
     return (ef > 0 ? ef : 1) - 1022;
 }
 
@@ -255,9 +303,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_split(const Params prm) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int P = prm.P;
     const int kr = blockIdx.x / prm.n_qc, qc = blockIdx.x - kr * prm.n_qc;
-    const int q0 = prm.q0[qc], Qw = prm.qw[qc], Qp = prm.Qp;
+    // (selects, not an indexed load: indexing the parameter arrays would
+    // copy the whole parameter block to local memory)
+    const int q0 = qc ? prm.q0[1] : prm.q0[0];
+    const int Qw = qc ? prm.qw[1] : prm.qw[0];
+    const int Qp = prm.Qp;
+    const double* __restrict__ Xg = prm.X;
+    const double* __restrict__ Yg = prm.Y;
+    const int64_t ldx = prm.ldx, ldy = prm.ldy, Ktot = prm.K;
     const int stacked = prm.stacked;
-    const Layout L = make_layout(P, Qp, stacked);
+    const Layout L = make_layout(P, Qp, Qw, stacked);
     const int NE = P + Qp;
     unsigned char* dig = smem + L.dig_off;
     double* acc = reinterpret_cast<double*>(smem + L.acc_off);
@@ -281,7 +336,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_split(const Params prm) {
     const int64_t nsteps = s_end > s_begin ? s_end - s_begin : 0;
 
     // ---- set-up: zero digit stages, accumulators, exponents; init barriers
-    for (uint32_t i = threadIdx.x * 16u; i < L.misc_off; i += NTHREADS * 16u)
+    for (uint32_t i = threadIdx.x * 16u; i < L.misc_off; i += NTHREADS * 16u)  // not the staging ring
         *reinterpret_cast<uint4*>(smem + i) = make_uint4(0, 0, 0, 0);
     __syncthreads();
     for (int i = threadIdx.x; i < NE; i += NTHREADS) e_run[i] = E_NONE;
@@ -313,49 +368,76 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_split(const Params prm) {
     if (warp < NCONV_WARPS) {
         // ================================================= converters
         const int ct = threadIdx.x;  // 0..255
-        const int units = 2 * (P + Qw);
+        const int units = L.units;
         const int per = (units + NCONV - 1) / NCONV;  // <= 2 for P + Qw <= 256
-        double cur[2][8], nxt[2][8];
-        auto load_step = [&](int64_t s, double (*dst)[8]) {
-            const int64_t row0 = (s_begin + s) * KSTEP;
+        const int nst = L.nst;
+        const uint32_t stg_a = smem_addr(smem + L.stg_off);
+        double cur[2][4];
+        // unit u: column c = u / 4, rows 8g + 4h .. 8g + 4h + 3 of the step
+        // with g = (u / 2) % 2, h = u % 2.  Stage element (row r of 4, unit
+        // u) of ring slot `slot` sits at stg_off + slot * stg_bytes +
+        // (r * units + u) * 8: a thread reads back exactly what it copied, so
+        // no barrier guards the ring
+        auto issue_step = [&](int64_t s) {
+            if (s < nsteps) {
+                const int64_t row0 = (s_begin + s) * KSTEP;
+                const uint32_t base = stg_a + (uint32_t)(s % nst) * L.stg_bytes;
+#pragma unroll
+                for (int it = 0; it < 2; ++it) {
+                    const int u = ct + it * NCONV;
+                    if (!(it < per && u < units)) continue;
+                    const int c = u >> 2, rb = (u & 3) * 4;
+                    const double* col;
+                    int64_t ld;
+                    if (c < P) {
+                        col = Xg + c;
+                        ld = ldx;
+                    } else {
+                        col = Yg + q0 + (c - P);
+                        ld = ldy;
+                    }
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int64_t k = row0 + rb + r;
+                        const bool ok = k < Ktot;
+                        cp_async8(base + (uint32_t)((r * units + u) * 8), col + (ok ? k : 0) * ld, ok);
+                    }
+                }
+            }
+            cp_async_commit();  // one group per step, empty or not
+        };
+        auto read_step = [&](int64_t s) {
+            const double* base = reinterpret_cast<const double*>(smem + L.stg_off + (uint32_t)(s % nst) * L.stg_bytes);
 #pragma unroll
             for (int it = 0; it < 2; ++it) {
                 const int u = ct + it * NCONV;
                 const bool valid = it < per && u < units;
-                const int c = u >> 1, g = u & 1;
-                const double* base;
-                int64_t ld;
-                if (c < P) {
-                    base = prm.X + c;
-                    ld = prm.ldx;
-                } else {
-                    base = prm.Y + q0 + (c - P);
-                    ld = prm.ldy;
-                }
 #pragma unroll
-                for (int r = 0; r < 8; ++r) {
-                    const int64_t k = row0 + g * 8 + r;
-                    dst[it][r] = (valid && k < prm.K) ? __ldg(base + k * ld) : 0.0;
-                }
+                for (int r = 0; r < 4; ++r) cur[it][r] = valid ? base[r * units + u] : 0.0;
             }
         };
+        for (int i = 0; i < nst - 1; ++i) issue_step(i);
         int64_t tile = -1;
         int steps_in_tile = TILE_STEPS;
         int slot = 0;
-        if (nsteps > 0) load_step(0, cur);
         for (int64_t s = 0; s < nsteps; ++s) {
-            if (s + 1 < nsteps) load_step(s + 1, nxt);
+            issue_step(s + nst - 1);
+            cp_async_wait(nst - 1);
+            read_step(s);
             // -- phase 1: column exponents of this step, running maxima
             if (ct == 0) brk[(s + 1) & 1] = 0;  // read by everyone before the previous barrier
 #pragma unroll
             for (int it = 0; it < 2; ++it) {
-                int em = E_NONE;
+                uint32_t hm = 0;
 #pragma unroll
-                for (int r = 0; r < 8; ++r) em = max(em, exp_of(cur[it][r]));
-                em = max(em, __shfl_xor_sync(0xffffffffu, em, 1));
+                for (int r = 0; r < 4; ++r)
+                    hm = max(hm, (uint32_t)((unsigned long long)__double_as_longlong(cur[it][r]) >> 32) & 0x7FFFFFFFu);
+                hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, 1));  // the four units of a column
+                hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, 2));  // are adjacent lanes
+                const int em = exp_from_hi(hm);
                 const int u = ct + it * NCONV;
-                if (it < per && u < units && (u & 1) == 0) {
-                    const int c = u >> 1;
+                if (it < per && u < units && (u & 3) == 0) {
+                    const int c = u >> 2;
                     if (em > e_run[c]) {
                         e_run[c] = em;
                         brk[s & 1] = 1;
@@ -389,10 +471,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_split(const Params prm) {
             }
             if (!ok) {
                 *abort_flag = 1;  // the others stop at the next barrier
-#pragma unroll
-                for (int it = 0; it < 2; ++it)
-#pragma unroll
-                    for (int r = 0; r < 8; ++r) cur[it][r] = nxt[it][r];
                 continue;
             }
             // -- phase 2: six bf16 slices of every value into the digit stage
@@ -401,15 +479,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_split(const Params prm) {
             for (int it = 0; it < 2; ++it) {
                 const int u = ct + it * NCONV;
                 if (!(it < per && u < units)) continue;
-                const int c = u >> 1, g = u & 1;
+                const int c = u >> 2, g = (u >> 1) & 1, hb = (u & 1) * 8;
                 const int e = e_run[c];
-                uint32_t w[NSLICE][4];
+                uint32_t w[NSLICE][2];
 #pragma unroll
-                for (int r = 0; r < 8; r += 2) {
+                for (int r = 0; r < 4; r += 2) {
                     float fa[NSLICE], fb[NSLICE];
-                    const bool na = split6(cur[it][r], e, fa);
-                    const bool nb = split6(cur[it][r + 1], e, fb);
-                    const uint32_t sg = (na ? 0x8000u : 0u) | (nb ? 0x80000000u : 0u);
+                    const uint32_t na = split6(cur[it][r], e, fa);
+                    const uint32_t nb = split6(cur[it][r + 1], e, fb);
+                    const uint32_t sg = (na >> 16) | nb;
 #pragma unroll
                     for (int sl = 0; sl < NSLICE; ++sl)
                         w[sl][r >> 1] = __byte_perm(__float_as_uint(fa[sl]), __float_as_uint(fb[sl]), 0x7632) ^ sg;
@@ -420,26 +498,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_split(const Params prm) {
                     for (int sl = 0; sl < NSLICE; ++sl) {
                         const int blk = stacked ? (sl >> 1) : sl;
                         const int row = (stacked ? (sl & 1) * 64 : 0) + c;
-                        *reinterpret_cast<uint4*>(stage + blk * 4096 + kmajor_off(row, g)) =
-                            make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
+                        *reinterpret_cast<uint2*>(stage + blk * 4096 + kmajor_off(row, g) + hb) =
+                            make_uint2(w[sl][0], w[sl][1]);
                     }
                 } else {
                     const int q = c - P;
 #pragma unroll
                     for (int sl = 0; sl < NSLICE; ++sl)
-                        *reinterpret_cast<uint4*>(stage + L.a_bytes + kmajor_off(sl * Qp + q, g)) =
-                            make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
+                        *reinterpret_cast<uint2*>(stage + L.a_bytes + kmajor_off(sl * Qp + q, g) + hb) =
+                            make_uint2(w[sl][0], w[sl][1]);
                 }
             }
             if (ct == 0) meta[d] = (new_tile ? 1 : 0) | (slot << 1);
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(bar(M_DIG_FULL + 8 * d));
-#pragma unroll
-            for (int it = 0; it < 2; ++it)
-#pragma unroll
-                for (int r = 0; r < 8; ++r) cur[it][r] = nxt[it][r];
         }
+        cp_async_wait(0);  // no copy may land after the CTA exits
     } else if (warp == MMA_WARP) {
         // ================================================= MMA issuer
         if (lane == 0) {
@@ -694,7 +769,7 @@ extern "C" tsm_status tsm_tsmttsm_split(tsm_op opA, tsm_dtype dtype, int M, int 
     if ((st = workspace_get(s, part + 256, 1, &ws)) != TSM_OK) return st;
     prm.ws = ws->partials;
     prm.err = reinterpret_cast<int*>(ws->tickets) + 32;  // error word of this stream
-    const split::Layout L = split::make_layout(P, prm.Qp, prm.stacked);
+    const split::Layout L = split::make_layout(P, prm.Qp, qmax, prm.stacked);
     if (L.total > di.smem_optin) return TSM_ERR_NOT_SUPPORTED;
     if (cudaFuncSetAttribute(split::k_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) !=
         cudaSuccess)
