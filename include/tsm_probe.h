@@ -29,14 +29,17 @@ tsm_status tsm_probe_fp64(int mode, int64_t iters, double *gflops, tsm_stream_t 
 /*
  * Memory bandwidth in GB/s over a caller-owned DEVICE buffer of `bytes`
  * bytes (16-byte aligned, multiple of 16).  mode 0: read-only thread-local
- * sum (the TSMTTSM-like stream); mode 1: in-place scale x = 1.0 * x (one read
- * and one write stream, TSMM-like; bytes counted twice).  `ilp` independent
- * 16-byte loads in flight per thread (1, 4 or 16: the load parallelism of the
- * paper's Table 1); `blocks_per_sm` CTAs of 256 threads per SM (0 = full
- * occupancy).  The buffer's contents are preserved by mode 1.
+ * sum (the TSMTTSM-like stream; loaded bits are folded with integer XOR so
+ * the FP64 pipe does not limit it); mode 1: in-place scale x = 1.0 * x (one
+ * read and one write stream, TSMM-like; bytes counted twice).  `ilp`
+ * independent 16-byte loads in flight per thread (1, 4 or 16: the load
+ * parallelism of the paper's Table 1); `blocks` CTAs in total (0 = 8 per SM)
+ * of `threads` threads each (0 = 256; otherwise a multiple of 32 in
+ * [32, 1024]), which sets the occupancy.  Best of four timed passes.  The
+ * buffer's contents are preserved by mode 1.
  */
 tsm_status tsm_probe_bandwidth(void *buffer, size_t bytes, int mode, int ilp,
-                               int blocks_per_sm, double *gbs, tsm_stream_t stream);
+                               int blocks, int threads, double *gbs, tsm_stream_t stream);
 
 #ifdef __cplusplus
 }

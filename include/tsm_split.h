@@ -9,7 +9,7 @@
  * ("Error-free transformations of matrix multiplication by using fast
  * routines of matrix multiplication and its applications", Numer. Algorithms
  * 59, 2012): every input column is scaled by a power of two and cut into six
- * signed 8-bit integer slices held exactly in bfloat16, the slice products
+ * signed 8-bit integer slices held exactly in fp16, the slice products
  * run on the tensor cores (tcgen05, FP32 accumulation in tensor memory kept
  * exact by bounding the rows per accumulation tile), and the slice products
  * are recombined and reduced over K in binary64.  Complex data is handled

@@ -196,6 +196,7 @@ __device__ void tsmm_item(const Inst& in, const Item& it, double* cs) {
     }
     __syncthreads();
     const int r = threadIdx.x / TPR, q = threadIdx.x - r * TPR;
+    const int npt = (N + TPR - 1) / TPR;  // result slots in use, <= NPT
     const int64_t sa = in.lda * CC, sb = in.ldo * CC;
     for (int64_t base = it.r0; base < it.r1; base += (int64_t)RPC * U) {
         int64_t row[U];
@@ -213,26 +214,40 @@ __device__ void tsmm_item(const Inst& in, const Item& it, double* cs) {
             for (int j = 0; j < NPT; ++j)
 #pragma unroll
                 for (int c = 0; c < CC; ++c) acc[u][j][c] = 0.0;
-        for (int m = 0; m < M; ++m) {
-            double av[U][CC];
+        // four columns of A per pass, their loads issued before the FMAs, so
+        // each thread keeps 4 * U independent loads in flight
+        for (int m0 = 0; m0 < M; m0 += 4) {
+            double av[4][U][CC];
 #pragma unroll
-            for (int u = 0; u < U; ++u)
+            for (int mm = 0; mm < 4; ++mm)
 #pragma unroll
-                for (int c = 0; c < CC; ++c) av[u][c] = rok[u] ? __ldg(in.A + row[u] * sa + m * CC + c) : 0.0;
+                for (int u = 0; u < U; ++u)
 #pragma unroll
-            for (int j = 0; j < NPT; ++j) {
-                const int n = q + j * TPR;
-                if (n < N) {
-                    const double cr = cs[(m * N + n) * CC], ci = cs[(m * N + n) * CC + CC - 1];
+                    for (int c = 0; c < CC; ++c)
+                        av[mm][u][c] = (rok[u] && m0 + mm < M) ? __ldg(in.A + row[u] * sa + (m0 + mm) * CC + c) : 0.0;
 #pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        if (!CPLX) {
-                            acc[u][j][0] = fma(av[u][0], cr, acc[u][j][0]);
-                        } else {
-                            acc[u][j][0] = fma(av[u][0], cr, acc[u][j][0]);
-                            acc[u][j][0] = fma(-av[u][CC - 1], ci, acc[u][j][0]);
-                            acc[u][j][CC - 1] = fma(av[u][0], ci, acc[u][j][CC - 1]);
-                            acc[u][j][CC - 1] = fma(av[u][CC - 1], cr, acc[u][j][CC - 1]);
+            for (int mm = 0; mm < 4; ++mm) {
+                const int m = m0 + mm;
+                if (m >= M) break;
+#pragma unroll
+                for (int j = 0; j < NPT; ++j) {
+                    // CTA-uniform bound: result slots no thread needs are
+                    // branched around (predicated-off FMAs still occupy the
+                    // FP64 pipe); only the last, ragged slot is guarded
+                    if (j >= npt) break;
+                    const int n = q + j * TPR;
+                    if (n < N) {
+                        const double cr = cs[(m * N + n) * CC], ci = cs[(m * N + n) * CC + CC - 1];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            if (!CPLX) {
+                                acc[u][j][0] = fma(av[mm][u][0], cr, acc[u][j][0]);
+                            } else {
+                                acc[u][j][0] = fma(av[mm][u][0], cr, acc[u][j][0]);
+                                acc[u][j][0] = fma(-av[mm][u][CC - 1], ci, acc[u][j][0]);
+                                acc[u][j][CC - 1] = fma(av[mm][u][0], ci, acc[u][j][CC - 1]);
+                                acc[u][j][CC - 1] = fma(av[mm][u][CC - 1], cr, acc[u][j][CC - 1]);
+                            }
                         }
                     }
                 }
@@ -244,6 +259,7 @@ __device__ void tsmm_item(const Inst& in, const Item& it, double* cs) {
             double* out = in.out + row[u] * sb;
 #pragma unroll
             for (int j = 0; j < NPT; ++j) {
+                if (j >= npt) break;
                 const int n = q + j * TPR;
                 if (n >= N) continue;
                 double vr = acc[u][j][0], vi = acc[u][j][CC - 1];
@@ -267,13 +283,27 @@ __device__ void tsmm_item(const Inst& in, const Item& it, double* cs) {
 
 // -------------------------------------------------------- persistent kernel
 
+// Accumulators stay at <= 32 doubles per thread in every instantiation
+// (complex data has no 4x8 / 8x4 tile and no 4-threads-per-row TSMM).
 template <bool CPLX, bool CONJ>
 __device__ void run_tsmttsm(const Inst& in, const Item& it, double* parts, unsigned* tickets, double* red) {
     switch (in.code) {
         case 1: tsmttsm_item<1, 1, 4, CPLX, CONJ>(in, it, parts, tickets, red); break;
         case 2: tsmttsm_item<2, 2, 2, CPLX, CONJ>(in, it, parts, tickets, red); break;
-        case 4: tsmttsm_item<4, 8, 1, CPLX, CONJ>(in, it, parts, tickets, red); break;
-        case 5: tsmttsm_item<8, 4, 1, CPLX, CONJ>(in, it, parts, tickets, red); break;
+        case 4:
+            if (!CPLX) {
+                tsmttsm_item<4, 8, 1, CPLX, CONJ>(in, it, parts, tickets, red);
+                break;
+            }
+            tsmttsm_item<4, 4, 1, CPLX, CONJ>(in, it, parts, tickets, red);
+            break;
+        case 5:
+            if (!CPLX) {
+                tsmttsm_item<8, 4, 1, CPLX, CONJ>(in, it, parts, tickets, red);
+                break;
+            }
+            tsmttsm_item<4, 4, 1, CPLX, CONJ>(in, it, parts, tickets, red);
+            break;
         default: tsmttsm_item<4, 4, 1, CPLX, CONJ>(in, it, parts, tickets, red); break;
     }
 }
@@ -281,7 +311,13 @@ __device__ void run_tsmttsm(const Inst& in, const Item& it, double* parts, unsig
 template <bool CPLX>
 __device__ void run_tsmm(const Inst& in, const Item& it, double* cs) {
     switch (in.code) {
-        case 1: tsmm_item<4, 16, CPLX>(in, it, cs); break;
+        case 1:
+            if (!CPLX) {
+                tsmm_item<4, 16, CPLX>(in, it, cs);
+                break;
+            }
+            tsmm_item<8, 8, CPLX>(in, it, cs);
+            break;
         case 3: tsmm_item<16, 4, CPLX>(in, it, cs); break;
         default: tsmm_item<8, 8, CPLX>(in, it, cs); break;
     }
@@ -317,7 +353,7 @@ __global__ void __launch_bounds__(kThreads) k_batched(const Inst* __restrict__ i
 }
 
 // TSMTTSM tiles by code and the default choice: least padding waste, then
-// the larger tile (capped at 16 accumulator doubles), thread count <= 256.
+// the larger tile (capped at 32 accumulator doubles), thread count <= 256.
 const int kTile[6][2] = {{0, 0}, {1, 1}, {2, 2}, {4, 4}, {4, 8}, {8, 4}};
 
 bool tile_ok(int code, int M, int N) {
@@ -333,7 +369,7 @@ int default_tile(int M, int N, int cplx) {
     for (int c = 1; c <= 5; ++c) {
         if (!tile_ok(c, M, N)) continue;
         const int tm = kTile[c][0], tn = kTile[c][1];
-        if (tm * tn * (cplx ? 2 : 1) > 16) continue;
+        if (tm * tn * (cplx ? 2 : 1) > 32) continue;
         const double waste = (double)((M + tm - 1) / tm * tm) * ((N + tn - 1) / tn * tn) / ((double)M * N);
         if (waste < bw - 1e-9 || (waste < bw + 1e-9 && tm * tn > ba)) {
             best = c;

@@ -173,6 +173,7 @@ __global__ void __launch_bounds__(kBlock) k_tsmm(const TsmmArgs a) {
     tsmm_stage_c<CC>(a, cs);
 
     const int r = threadIdx.x / TPR, q = threadIdx.x - r * TPR;
+    const int npt = (N + TPR - 1) / TPR;  // result slots in use, <= NPT
     const double* __restrict__ A = a.A;
     const int64_t sa = a.lda * CC, sb = a.ldb * CC;
     const int64_t step = (int64_t)gridDim.x * RPC * U;
@@ -201,6 +202,9 @@ __global__ void __launch_bounds__(kBlock) k_tsmm(const TsmmArgs a) {
                 for (int c = 0; c < CC; ++c) av[u][c] = rok[u] ? __ldg(A + row[u] * sa + m * CC + c) : 0.0;
 #pragma unroll
             for (int j = 0; j < NPT; ++j) {
+                // CTA-uniform bound: unused result slots are branched around
+                // (predicated-off FMAs still occupy the FP64 pipe)
+                if (j >= npt) break;
                 const int n = q + j * TPR;
                 if (n < N) {
                     const double cr = cs[(m * N + n) * CC];
@@ -226,6 +230,7 @@ __global__ void __launch_bounds__(kBlock) k_tsmm(const TsmmArgs a) {
             double* out = a.B + row[u] * sb;
 #pragma unroll
             for (int j = 0; j < NPT; ++j) {
+                if (j >= npt) break;
                 const int n = q + j * TPR;
                 if (n >= N) continue;
                 tsmm_store<CC>(a, out, n, acc[u][j][0], acc[u][j][CC - 1]);

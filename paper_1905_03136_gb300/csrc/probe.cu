@@ -139,15 +139,15 @@ extern "C" tsm_status tsm_probe_fp64(int mode, int64_t iters, double* gflops, ts
     return TSM_OK;
 }
 
-extern "C" tsm_status tsm_probe_bandwidth(void* buffer, size_t bytes, int mode, int ilp, int blocks_per_sm,
-                                          double* gbs, tsm_stream_t stream) {
+extern "C" tsm_status tsm_probe_bandwidth(void* buffer, size_t bytes, int mode, int ilp, int blocks_in,
+                                          int threads_in, double* gbs, tsm_stream_t stream) {
     if (!buffer || !gbs || bytes < 16 || (bytes % 16) || ((uintptr_t)buffer % 16)) return TSM_ERR_INVALID_VALUE;
-    if ((mode != 0 && mode != 1) || (ilp != 1 && ilp != 4 && ilp != 16) || blocks_per_sm < 0)
-        return TSM_ERR_INVALID_VALUE;
+    if ((mode != 0 && mode != 1) || (ilp != 1 && ilp != 4 && ilp != 16) || blocks_in < 0) return TSM_ERR_INVALID_VALUE;
+    if (threads_in != 0 && (threads_in < 32 || threads_in > 1024 || threads_in % 32)) return TSM_ERR_INVALID_VALUE;
     cudaStream_t s = (cudaStream_t)stream;
     const int sm = device_info().sm_count;
-    const int bps = blocks_per_sm > 0 ? blocks_per_sm : 8;
-    const int blocks = sm * bps;
+    const int blocks = blocks_in > 0 ? blocks_in : sm * 8;
+    const int threads = threads_in > 0 ? threads_in : 256;
     const int64_t n = (int64_t)(bytes / 16);
     double* dummy = nullptr;
     if (cudaMalloc(&dummy, 64) != cudaSuccess) return TSM_ERR_ALLOC;
@@ -156,13 +156,13 @@ extern "C" tsm_status tsm_probe_bandwidth(void* buffer, size_t bytes, int mode, 
     for (int rep = 0; rep < 4; ++rep) {
         t.start();
         if (mode == 0) {
-            if (ilp == 1) k_read<1><<<blocks, 256, 0, s>>>((const double2*)buffer, n, dummy);
-            if (ilp == 4) k_read<4><<<blocks, 256, 0, s>>>((const double2*)buffer, n, dummy);
-            if (ilp == 16) k_read<16><<<blocks, 256, 0, s>>>((const double2*)buffer, n, dummy);
+            if (ilp == 1) k_read<1><<<blocks, threads, 0, s>>>((const double2*)buffer, n, dummy);
+            if (ilp == 4) k_read<4><<<blocks, threads, 0, s>>>((const double2*)buffer, n, dummy);
+            if (ilp == 16) k_read<16><<<blocks, threads, 0, s>>>((const double2*)buffer, n, dummy);
         } else {
-            if (ilp == 1) k_scale_stream<1><<<blocks, 256, 0, s>>>((double2*)buffer, n);
-            if (ilp == 4) k_scale_stream<4><<<blocks, 256, 0, s>>>((double2*)buffer, n);
-            if (ilp == 16) k_scale_stream<16><<<blocks, 256, 0, s>>>((double2*)buffer, n);
+            if (ilp == 1) k_scale_stream<1><<<blocks, threads, 0, s>>>((double2*)buffer, n);
+            if (ilp == 4) k_scale_stream<4><<<blocks, threads, 0, s>>>((double2*)buffer, n);
+            if (ilp == 16) k_scale_stream<16><<<blocks, threads, 0, s>>>((double2*)buffer, n);
         }
         const float ms = t.stop();
         if (ms > 0.f && ms < best) best = ms;

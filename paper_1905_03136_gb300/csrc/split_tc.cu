@@ -8,7 +8,7 @@
 //   x = 2^e * sum_s alpha_s * 2^(-7 - 8s),  s = 0..5, alpha_s integer, |alpha_s| <= 128
 //
 // where e is a running maximum exponent of x's column (|x| < 2^e), so every
-// alpha_s is exact in bfloat16.  Then, per accumulation tile of at most 256
+// alpha_s is exact in fp16 (11-bit significand).  Then, per accumulation tile of at most 256
 // rows in which no column exponent changes,
 //
 //   sum_k x_kp y_kq = 2^(e_p + e_q - 14) * sum_d 2^(-8d) P_d[p][q],
@@ -27,7 +27,7 @@
 //               global memory into a per-thread cp.async ring several steps
 //               ahead (loads of later steps are in flight while step s is
 //               converted: the paper's leap frogging, Sec. 3.1, made deep),
-//               update the running column exponents, and write the six bf16
+//               update the running column exponents, and write the six fp16
 //               slices into shared memory in the canonical K-major
 //               core-matrix layout of the MMA operands; one unit of work is
 //               4 rows of one column;
@@ -46,24 +46,24 @@
 #include <cstdint>
 #include <cstdio>
 
+#include <cuda_fp16.h>
+
 #include "tsm_internal.h"
 #include "tsm_split.h"
 
 namespace tsm {
 namespace split {
 
-constexpr int KSTEP = 16;           // rows per MMA (bf16: K = 16)
+constexpr int KSTEP = 16;           // rows per MMA (16-bit inputs: K = 16)
 constexpr int TILE_STEPS = 16;      // steps per exact accumulation tile (256 rows)
 constexpr int NSLICE = 6;           // 8-bit slices per input
 constexpr int NDIG = 2;             // digit stages (converters -> MMA)
 constexpr int NST_MAX = 8;          // FP64 staging stages (cp.async ring, per thread)
 constexpr int NEXP = 4;             // exponent snapshot ring (converters -> epilogue)
-constexpr int NCONV_WARPS = 16;
-constexpr int NCONV = NCONV_WARPS * 32;
-constexpr int MMA_WARP = 16;
-constexpr int EPI_WARP0 = 17;
+constexpr int MAX_CONV_WARPS = 16;  // converters: a per-shape multiple of 32 threads
+constexpr int NCONV_MAX = MAX_CONV_WARPS * 32;
 constexpr int NEPI_WARPS = 4;
-constexpr int NTHREADS = (EPI_WARP0 + NEPI_WARPS) * 32;  // 672
+constexpr int NTHREADS_MAX = (MAX_CONV_WARPS + 1 + NEPI_WARPS) * 32;  // 672
 constexpr int TMEM_COLS = 512;
 constexpr int E_NONE = -4000;       // running exponent before any nonzero value
 constexpr long long kDefaultTimeout = 4000000000ll;  // SM cycles (~2 s)
@@ -80,7 +80,9 @@ struct Params {
     int64_t steps_per_kr;
     int stacked;  // P <= 64
     int Qp;       // padded chunk width (multiple of 16)
-    double* ws;   // [n_kr][P][Q]
+    int nconv;    // converter threads (multiple of 32, <= NCONV_MAX); MMA warp and 4 epilogue warps follow
+    double* ws;     // [n_kr][P][Q]
+    double* flush;  // [CTA][Qp][128]: binary64 totals of the epilogue lanes
     int* err;
     long long timeout;
 };
@@ -146,12 +148,12 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
     return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
-// Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major,
-// M = 128, N as given.
+// Instruction descriptor of kind::f16: D = F32, A = B = F16 (format code 0),
+// both K-major, M = 128, N as given.
 __device__ __forceinline__ uint32_t instr_desc(int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t accumulate) {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
@@ -255,33 +257,47 @@ enum {
 
 // ------------------------------------------------------------ digit maths
 
-// Six balanced base-256 digits of |x| truncated to 47 fractional bits under
-// 2^e, each as a float (exact), most significant first: |x| 2^(47-e) ~ X =
-// sum_s d_s 2^(40-8s), d_0 in [0, 128], d_1..d_5 in [-128, 127].  Requires
-// |x| < 2^e.  Subnormals are handled exactly (no implicit bit).  Returns the
-// sign bit of x.
-//   X: the 53-bit significand shifted right by e + 1028 - max(ef, 1) >= 6
-//      (clamped to 63, which leaves 0 for values below the column's range);
-//   balanced digits: add 0x80 to each of the five low bytes (with carries),
-//      read the bytes back and remove the bias -- one PRMT places a byte into
-//      the float 2^23 + byte, one FADD removes 2^23 (+ 128).
-__device__ __forceinline__ uint32_t split6(double x, int e, float* f) {
+// |x| as a fixed-point integer with 47 bits below 2^e (truncated), plus the
+// five low bytes biased by 0x80 so that they read back as balanced digits:
+// returns Y = X + 0x8080808080 where X = floor(|x| 2^(47-e)) < 2^47.  The
+// six base-256 digits of X = sum_s d_s 2^(40-8s) are d_0 = byte 5 of Y in
+// [0, 128] and d_s = byte (5-s) of Y - 128 in [-128, 127] for s >= 1.
+// Requires |x| < 2^e; subnormals are exact (no implicit bit); values below
+// the column's range give 0 (the shift is clamped to 63).
+__device__ __forceinline__ unsigned long long fixed47(double x, int e, uint32_t* sign) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
     const uint32_t hi = (uint32_t)(bits >> 32);
+    *sign = hi & 0x80000000u;
     const int ef = (int)((hi >> 20) & 0x7FFu);
     const uint32_t mhi = (hi & 0xFFFFFu) | (ef ? 0x100000u : 0u);
     const unsigned long long mant = ((unsigned long long)mhi << 32) | (uint32_t)bits;
     const int sh = min(e + 1028 - max(ef, 1), 63);
-    const unsigned long long X = mant >> sh;
-    const unsigned long long Yb = X + 0x8080808080ull;
-    const uint32_t lo = (uint32_t)Yb, h8 = (uint32_t)(Yb >> 32);
-    f[0] = __uint_as_float(__byte_perm(h8, 0x4B000000u, 0x7541)) - 8388608.0f;   // top digit
-    f[1] = __uint_as_float(__byte_perm(h8, 0x4B000000u, 0x7540)) - 8388736.0f;   // byte 4 - 128
-    f[2] = __uint_as_float(__byte_perm(lo, 0x4B000000u, 0x7543)) - 8388736.0f;   // byte 3 - 128
-    f[3] = __uint_as_float(__byte_perm(lo, 0x4B000000u, 0x7542)) - 8388736.0f;   // byte 2 - 128
-    f[4] = __uint_as_float(__byte_perm(lo, 0x4B000000u, 0x7541)) - 8388736.0f;   // byte 1 - 128
-    f[5] = __uint_as_float(__byte_perm(lo, 0x4B000000u, 0x7540)) - 8388736.0f;   // byte 0 - 128
-    return hi & 0x80000000u;
+    return (mant >> sh) + 0x8080808080ull;
+}
+
+// The six fp16 slices of two values a (row r) and b (row r + 1) of one
+// column, packed per slice as (a, b) in one 32-bit word, sign applied.  A
+// digit byte placed under the fp16 exponent of 1024 (0x64XX) is 1024 + byte
+// exactly; one packed subtraction removes 1024 (+ 128) from both halves.
+__device__ __forceinline__ void split_pair(double xa, double xb, int e, uint32_t* w) {
+    uint32_t sa, sb;
+    const unsigned long long ya = fixed47(xa, e, &sa), yb = fixed47(xb, e, &sb);
+    const uint32_t alo = (uint32_t)ya, ahi = (uint32_t)(ya >> 32);
+    const uint32_t blo = (uint32_t)yb, bhi = (uint32_t)(yb >> 32);
+    const uint32_t sg = (sa >> 16) | sb;
+    const __half2 top = __halves2half2(__ushort_as_half(0x6400), __ushort_as_half(0x6400));  // 1024
+    const __half2 low = __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480));  // 1152
+    auto make = [&](uint32_t x, uint32_t y, uint32_t sel, __half2 bias) {
+        uint32_t u = (__byte_perm(x, y, sel) & 0x00FF00FFu) | 0x64006400u;
+        __half2 h = __hsub2(*reinterpret_cast<__half2*>(&u), bias);
+        return *reinterpret_cast<uint32_t*>(&h) ^ sg;
+    };
+    w[0] = make(ahi, bhi, 0x0501, top);  // byte 5
+    w[1] = make(ahi, bhi, 0x0400, low);  // byte 4
+    w[2] = make(alo, blo, 0x0703, low);  // byte 3
+    w[3] = make(alo, blo, 0x0602, low);  // byte 2
+    w[4] = make(alo, blo, 0x0501, low);  // byte 1
+    w[5] = make(alo, blo, 0x0400, low);  // byte 0
 }
 
 // Exponent from the largest magnitude high word of a column: |x| < 2^e for
@@ -299,7 +315,7 @@ __device__ __forceinline__ uint32_t kmajor_off(int r, int g) {
 
 // ------------------------------------------------------------ the kernel
 
-__global__ void __launch_bounds__(NTHREADS, 1) k_split(const Params prm) {
+__global__ void __launch_bounds__(NTHREADS_MAX, 1) k_split(const Params prm) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int P = prm.P;
     const int kr = blockIdx.x / prm.n_qc, qc = blockIdx.x - kr * prm.n_qc;
@@ -315,7 +331,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_split(const Params prm) {
     const Layout L = make_layout(P, Qp, Qw, stacked);
     const int NE = P + Qp;
     unsigned char* dig = smem + L.dig_off;
-    double* acc = reinterpret_cast<double*>(smem + L.acc_off);
+    double* acc = reinterpret_cast<double*>(smem + L.acc_off);  // epilogue integer sums (64-bit)
     int* e_run = reinterpret_cast<int*>(smem + L.exp_off);
     int* e_snap = e_run + NE;
     unsigned char* misc = smem + L.misc_off;
@@ -327,6 +343,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_split(const Params prm) {
     volatile int* tile_info = reinterpret_cast<volatile int*>(misc + M_TILE_INFO);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long tmo = prm.timeout;
+    const int NCONV = prm.nconv, NCONV_WARPS = NCONV / 32;
+    const int MMA_WARP = NCONV_WARPS, EPI_WARP0 = NCONV_WARPS + 1;
+    const int NTHREADS = blockDim.x;
 
     // K range of this CTA, in 16-row steps
     const int64_t steps_total = (prm.K + KSTEP - 1) / KSTEP;
@@ -369,7 +388,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_split(const Params prm) {
         // ================================================= converters
         const int ct = threadIdx.x;  // 0..255
         const int units = L.units;
-        const int per = (units + NCONV - 1) / NCONV;  // <= 2 for P + Qw <= 256
+        const int per = (units + NCONV - 1) / NCONV;  // <= 2 by the host's choice of NCONV
         const int nst = L.nst;
         const uint32_t stg_a = smem_addr(smem + L.stg_off);
         double cur[2][4];
@@ -446,7 +465,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_split(const Params prm) {
             }
             named_sync(1, NCONV);
             if (*abort_flag) break;  // uniform: set before this barrier by a failed warp
-            const bool new_tile = (brk[s & 1] != 0) || steps_in_tile >= TILE_STEPS;
+            const bool expchg = brk[s & 1] != 0;  // a column exponent grew: new scale
+            const bool new_tile = expchg || steps_in_tile >= TILE_STEPS;
             // waits are taken by lane 0 and broadcast, so failure is warp-uniform
             bool ok = true;
             if (new_tile) {
@@ -473,7 +493,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_split(const Params prm) {
                 *abort_flag = 1;  // the others stop at the next barrier
                 continue;
             }
-            // -- phase 2: six bf16 slices of every value into the digit stage
+            // -- phase 2: six fp16 slices of every value into the digit stage
             unsigned char* stage = dig + d * L.stage;
 #pragma unroll
             for (int it = 0; it < 2; ++it) {
@@ -484,13 +504,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_split(const Params prm) {
                 uint32_t w[NSLICE][2];
 #pragma unroll
                 for (int r = 0; r < 4; r += 2) {
-                    float fa[NSLICE], fb[NSLICE];
-                    const uint32_t na = split6(cur[it][r], e, fa);
-                    const uint32_t nb = split6(cur[it][r + 1], e, fb);
-                    const uint32_t sg = (na >> 16) | nb;
+                    uint32_t wp[NSLICE];
+                    split_pair(cur[it][r], cur[it][r + 1], e, wp);
 #pragma unroll
-                    for (int sl = 0; sl < NSLICE; ++sl)
-                        w[sl][r >> 1] = __byte_perm(__float_as_uint(fa[sl]), __float_as_uint(fb[sl]), 0x7632) ^ sg;
+                    for (int sl = 0; sl < NSLICE; ++sl) w[sl][r >> 1] = wp[sl];
                 }
                 if (c < P) {
                     // operand A: slice sl in block (stacked ? sl/2 : sl), row (stacked ? (sl&1)*64 : 0) + c
@@ -509,7 +526,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_split(const Params prm) {
                             make_uint2(w[sl][0], w[sl][1]);
                 }
             }
-            if (ct == 0) meta[d] = (new_tile ? 1 : 0) | (slot << 1);
+            if (ct == 0) meta[d] = (new_tile ? 1 : 0) | (expchg ? 2 : 0) | (slot << 2);
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(bar(M_DIG_FULL + 8 * d));
@@ -519,7 +536,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_split(const Params prm) {
         // ================================================= MMA issuer
         if (lane == 0) {
             int64_t tile = -1;
-            int cur_slot = 0;
+            int cur_slot = 0, cur_chg = 0;
             bool failed = false;
             uint32_t mma_phase = 0;
             const uint32_t dig_a = smem_addr(dig);
@@ -541,7 +558,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_split(const Params prm) {
                             break;
                         }
                         mma_phase ^= 1;
-                        *tile_info = cur_slot;
+                        *tile_info = cur_slot | (cur_chg << 10);
                         tc_fence_before();
                         mbar_arrive(bar(M_TILE_FULL));
                         if (!mbar_wait(bar(M_TMEM_EMPTY), (uint32_t)(tile & 1), tmo, prm.err, 5)) {
@@ -551,7 +568,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_split(const Params prm) {
                         tc_fence_after();
                     }
                     ++tile;
-                    cur_slot = m >> 1;
+                    cur_slot = m >> 2;
+                    cur_chg = (m >> 1) & 1;
                 }
                 const uint32_t sa = dig_a + (uint32_t)d * L.stage;
                 const uint32_t sb = sa + L.a_bytes;
@@ -566,7 +584,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_split(const Params prm) {
                         const uint64_t ad = smem_desc(sa + rb * 4096, 128, 256);
                         const uint64_t bd = smem_desc(sb + (uint32_t)(t0 * Qp * 32), 128, 256);
                         const uint32_t dcol = (uint32_t)((s_a + t0) * Qp);
-                        mma_bf16(tmem + dcol, ad, bd, instr_desc(cnt * Qp), (rb == 0 && new_tile) ? 0u : 1u);
+                        mma_f16(tmem + dcol, ad, bd, instr_desc(cnt * Qp), (rb == 0 && new_tile) ? 0u : 1u);
                     }
                 }
                 mma_commit(bar(M_DIG_EMPTY + 8 * d));
@@ -575,7 +593,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_split(const Params prm) {
             mma_commit(bar(M_MMA_DONE));
             const bool drained = mbar_wait(bar(M_MMA_DONE), mma_phase, kDefaultTimeout, prm.err, 6);
             if (!failed && drained && tile >= 0) {
-                *tile_info = cur_slot | (1 << 8);
+                *tile_info = cur_slot | (1 << 8) | (cur_chg << 10);
                 tc_fence_before();
                 mbar_arrive(bar(M_TILE_FULL));
             } else if (tile < 0 && !failed) {
@@ -586,18 +604,47 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_split(const Params prm) {
         __syncwarp();
     } else {
         // ================================================= epilogue
+        // Per (lane, column): an exact 64-bit integer sum of the tiles' W in
+        // shared memory, at the scale of the current column exponents.  It
+        // moves to binary64 (`flush`, this thread's own entries in global
+        // memory) only when an exponent grows, when the integer sum would
+        // overflow, and at the end -- not once per tile.
         const int ew = warp - EPI_WARP0;
         const int lane_base = 32 * (warp & 3);
         const int row = lane_base + lane;  // TMEM lane = accumulator row
         const int p = stacked ? (row & 63) : row;
         const int half = stacked ? (row >> 6) : 0;
         const bool prow = p < P;
+        long long* iacc = reinterpret_cast<long long*>(acc);
+        double* flush = prm.flush + (int64_t)blockIdx.x * Qp * 128;
+        for (int q = 0; q < Qp; ++q) flush[q * 128 + row] = 0.0;
+        auto scaled = [](long long a, int E) {
+            return (E >= -1022 && E <= 1023) ? (double)a * __longlong_as_double((long long)(E + 1023) << 52)
+                                             : scalbn((double)a, E);
+        };
+        auto flush_all = [&](const int* exs) {
+            if (!prow) return;
+            const int epf = exs[p];
+            for (int q = 0; q < Qw; ++q) {
+                const long long a = iacc[q * 128 + row];
+                if (a == 0) continue;
+                iacc[q * 128 + row] = 0;
+                flush[q * 128 + row] += scaled(a, epf + exs[P + q] - 54);
+            }
+        };
+        int prev_slot = -1;
         for (int64_t tile = 0;; ++tile) {
             if (!mbar_wait(bar(M_TILE_FULL), (uint32_t)(tile & 1), tmo, prm.err, 7)) break;
             tc_fence_after();
             const int info = *tile_info;
             if (info & (1 << 9)) break;
             const int slot = info & 0xFF;
+            const bool chg = (info >> 10) & 1;
+            if (prev_slot >= 0) {
+                if (chg) flush_all(e_snap + prev_slot * NE);  // sums so far carry the old scale
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar(M_EXP_EMPTY + 8 * prev_slot));
+            }
             const int* ex = e_snap + slot * NE;
             const int ep = prow ? ex[p] : 0;
             for (int qb = 0; qb < Qp; qb += 8) {
@@ -618,21 +665,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_split(const Params prm) {
                             W += (long long)__float2int_rn(__uint_as_float(v[j][qq])) << (8 * (NSLICE - 1 - dd));
                     }
                     if (W == 0) continue;
-                    const int E = ep + ex[P + q] - 54;
-                    double* a_ = &acc[q * 128 + row];
-                    if (E >= -1022 && E <= 1023)
-                        *a_ = fma((double)W, __longlong_as_double((long long)(E + 1023) << 52), *a_);
-                    else
-                        *a_ += scalbn((double)W, E);
+                    long long* ap = &iacc[q * 128 + row];
+                    const long long a = *ap;
+                    long long sum = (long long)((unsigned long long)a + (unsigned long long)W);
+                    if (((a ^ sum) & (W ^ sum)) < 0) {  // would overflow: move a to binary64
+                        flush[q * 128 + row] += scaled(a, ep + ex[P + q] - 54);
+                        sum = W;
+                    }
+                    *ap = sum;
                 }
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(bar(M_TMEM_EMPTY));
-                mbar_arrive(bar(M_EXP_EMPTY + 8 * slot));
+            if (lane == 0) mbar_arrive(bar(M_TMEM_EMPTY));
+            prev_slot = slot;
+            if (info & (1 << 8)) {
+                flush_all(ex);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar(M_EXP_EMPTY + 8 * slot));
+                break;
             }
-            if (info & (1 << 8)) break;
         }
         (void)ew;
     }
@@ -640,10 +692,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_split(const Params prm) {
     __syncthreads();
     // CTA partial: G[p][q0 + q] for this K range
     double* out = prm.ws + (int64_t)kr * P * prm.Q;
+    const double* fl = prm.flush + (int64_t)blockIdx.x * Qp * 128;
     for (int i = threadIdx.x; i < P * Qw; i += NTHREADS) {
         const int pp = i / Qw, q = i - pp * Qw;
-        double v = acc[q * 128 + pp];
-        if (stacked) v += acc[q * 128 + 64 + pp];
+        double v = fl[q * 128 + pp];
+        if (stacked) v += fl[q * 128 + 64 + pp];
         out[(int64_t)pp * prm.Q + q0 + q] = v;
     }
     tc_fence_before();
@@ -766,16 +819,28 @@ extern "C" tsm_status tsm_tsmttsm_split(tsm_op opA, tsm_dtype dtype, int M, int 
 
     Workspace* ws = nullptr;
     const size_t part = (size_t)n_kr * P * Q * sizeof(double);
-    if ((st = workspace_get(s, part + 256, 1, &ws)) != TSM_OK) return st;
+    const size_t flush = (size_t)n_kr * prm.n_qc * prm.Qp * 128 * sizeof(double);
+    if ((st = workspace_get(s, part + flush + 256, 1, &ws)) != TSM_OK) return st;
     prm.ws = ws->partials;
+    prm.flush = ws->partials + (size_t)n_kr * P * Q;
     prm.err = reinterpret_cast<int*>(ws->tickets) + 32;  // error word of this stream
     const split::Layout L = split::make_layout(P, prm.Qp, qmax, prm.stacked);
+    // converters: the fewest rounds of units, spread evenly over a multiple
+    // of 32 threads
+    {
+        const int units = L.units;
+        const int rounds = (units + split::NCONV_MAX - 1) / split::NCONV_MAX;
+        int nconv = (units + rounds - 1) / rounds;
+        nconv = (nconv + 31) & ~31;
+        if (nconv > split::NCONV_MAX) nconv = split::NCONV_MAX;
+        prm.nconv = nconv;
+    }
     if (L.total > di.smem_optin) return TSM_ERR_NOT_SUPPORTED;
     if (cudaFuncSetAttribute(split::k_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) !=
         cudaSuccess)
         return TSM_ERR_LAUNCH;
     if (cudaMemsetAsync(prm.err, 0, sizeof(int), s) != cudaSuccess) return TSM_ERR_LAUNCH;
-    split::k_split<<<n_kr * prm.n_qc, split::NTHREADS, L.total, s>>>(prm);
+    split::k_split<<<n_kr * prm.n_qc, prm.nconv + (1 + split::NEPI_WARPS) * 32, L.total, s>>>(prm);
     if (cudaGetLastError() != cudaSuccess) return TSM_ERR_LAUNCH;
     const int outs = M * N;
     split::k_split_combine<<<(outs + 127) / 128, 128, 0, s>>>(

@@ -8,7 +8,8 @@ _lib.extend_signatures({
     "tsm_probe_fp64": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
                                       ctypes.c_void_p]),
     "tsm_probe_bandwidth": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
-                                           ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+                                           ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.c_void_p]),
 })
 
 
@@ -25,11 +26,12 @@ def fp64_peak(mode=0, iters=20000, stream=None):
     return out.value
 
 
-def bandwidth(buf, mode=0, ilp=16, blocks_per_sm=0, stream=None):
-    """Measured GB/s over a device tensor (mode 0 read-only, 1 scale)."""
+def bandwidth(buf, mode=0, ilp=16, blocks=0, threads=0, stream=None):
+    """Measured GB/s over a device tensor (mode 0 read-only, 1 scale);
+    blocks = CTAs in total (0: 8 per SM), threads per CTA (0: 256)."""
     out = ctypes.c_double()
     nbytes = buf.numel() * buf.element_size()
     nbytes -= nbytes % 16
-    _lib.call("tsm_probe_bandwidth", ctypes.c_void_p(buf.data_ptr()), nbytes, mode, ilp, blocks_per_sm,
+    _lib.call("tsm_probe_bandwidth", ctypes.c_void_p(buf.data_ptr()), nbytes, mode, ilp, blocks, threads,
               ctypes.byref(out), _stream(stream))
     return out.value
