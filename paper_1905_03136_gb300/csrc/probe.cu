@@ -43,24 +43,29 @@ __global__ void k_dmma_peak(int64_t iters, double seed, double* out) {
     if (s == 12345.678) out[0] = s;
 }
 
-// Read-only stream: the loaded bits are folded with integer XOR so that
-// the FP64 pipe (slow on this part) never limits the measured bandwidth.
+// Read-only stream.  Each CTA takes contiguous chunks of ILP x blockDim
+// 16-byte vectors (chunk c, then c + gridDim.x, ...), so the ILP loads a
+// thread keeps in flight are coalesced and fall in the same DRAM pages.
+// The loaded bits are folded with integer XOR so that the FP64 pipe (slow
+// on this part) never limits the measured bandwidth.
 template <int ILP>
 __global__ void k_read(const double2* __restrict__ x, int64_t n, double* out) {
     unsigned long long s0 = 0, s1 = 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    for (; i + (ILP - 1) * stride < n; i += ILP * stride) {
+    const int64_t chunk = (int64_t)ILP * blockDim.x;
+    const int64_t nfull = n / chunk;
+    for (int64_t c = blockIdx.x; c < nfull; c += gridDim.x) {
+        const double2* p = x + c * chunk + threadIdx.x;
         double2 v[ILP];
 #pragma unroll
-        for (int u = 0; u < ILP; ++u) v[u] = __ldcs(x + i + u * stride);
+        for (int u = 0; u < ILP; ++u) v[u] = __ldcs(p + u * blockDim.x);
 #pragma unroll
         for (int u = 0; u < ILP; ++u) {
             s0 ^= __double_as_longlong(v[u].x);
             s1 ^= __double_as_longlong(v[u].y);
         }
     }
-    for (; i < n; i += stride) {
+    for (int64_t i = nfull * chunk + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
         const double2 v = __ldcs(x + i);
         s0 ^= __double_as_longlong(v.x);
         s1 ^= __double_as_longlong(v.y);
@@ -68,18 +73,23 @@ __global__ void k_read(const double2* __restrict__ x, int64_t n, double* out) {
     if ((s0 ^ s1) == 0x123456789abcdefull) out[0] = (double)s0;
 }
 
+// Read-modify-write stream with the same chunking (the STREAM "scale"
+// kernel with factor 1, which leaves the buffer unchanged).
 template <int ILP>
 __global__ void k_scale_stream(double2* x, int64_t n) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    for (; i + (ILP - 1) * stride < n; i += ILP * stride) {
+    const int64_t chunk = (int64_t)ILP * blockDim.x;
+    const int64_t nfull = n / chunk;
+    for (int64_t c = blockIdx.x; c < nfull; c += gridDim.x) {
+        double2* p = x + c * chunk + threadIdx.x;
         double2 v[ILP];
 #pragma unroll
-        for (int u = 0; u < ILP; ++u) v[u] = __ldcs(x + i + u * stride);
+        for (int u = 0; u < ILP; ++u) v[u] = __ldcs(p + u * blockDim.x);
 #pragma unroll
-        for (int u = 0; u < ILP; ++u) __stcs(x + i + u * stride, make_double2(v[u].x * 1.0, v[u].y * 1.0));
+        for (int u = 0; u < ILP; ++u) __stcs(p + u * blockDim.x, make_double2(v[u].x * 1.0, v[u].y * 1.0));
     }
-    for (; i < n; i += stride) __stcs(x + i, __ldcs(x + i));
+    for (int64_t i = nfull * chunk + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        __stcs(x + i, __ldcs(x + i));
 }
 
 struct Timer {

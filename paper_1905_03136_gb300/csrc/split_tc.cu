@@ -18,22 +18,30 @@
 // exact in FP32 for d <= 3 (<= 2^24), and within a few FP32 units for
 // d = 4, 5 whose weight is below 2^-46.  The tensor cores form all P_d in
 // tensor memory; the epilogue converts them to one exact 64-bit integer
-// W = sum_d P_d 2^(8(5-d)) per entry and accumulates W * 2^(e_p+e_q-54) in
-// binary64.  Partials of all CTAs are reduced in a fixed order.
+// W = sum_d P_d 2^(8(5-d)) per entry and sums W exactly in 64-bit integers
+// across tiles, moving the sum to binary64 only when a column exponent
+// grows, when it would overflow, and at the end.  Partials of all CTAs are
+// reduced in a fixed order.
 //
 // CTA organisation (one CTA per SM, persistent over a contiguous K range and
 // a chunk of Y's columns):
-//   warps 0-15  converters: stage upcoming 16-row steps of X and Y from
-//               global memory into a per-thread cp.async ring several steps
-//               ahead (loads of later steps are in flight while step s is
-//               converted: the paper's leap frogging, Sec. 3.1, made deep),
-//               update the running column exponents, and write the six fp16
-//               slices into shared memory in the canonical K-major
-//               core-matrix layout of the MMA operands; one unit of work is
-//               4 rows of one column;
-//   warp 16     allocates tensor memory and issues tcgen05.mma (one thread);
-//   warps 17-20 epilogue: drain tensor memory after each tile (tcgen05.ld),
-//               recombine, accumulate in binary64 in shared memory.
+//   converter warps  each thread owns one or two fixed "units" (4 rows of
+//                    one column in every 16-row step) and keeps the global
+//                    loads of its next one or two steps in flight in
+//                    registers (the paper's leap frogging, Sec. 3.1, made
+//                    deep); it keeps its columns' running exponents in
+//                    registers and writes the six fp16 slices of its values
+//                    into a ring of digit stages in the canonical K-major
+//                    core-matrix layout of the MMA operands.  The warps do
+//                    not synchronise with one another: a warp whose column
+//                    exponent grew stamps the stage with the step index;
+//   MMA warp         allocates tensor memory; lane 0 issues tcgen05.mma and
+//                    decides the tile boundaries (a stamped stage, or 16
+//                    steps); the warp copies the tile's exponents for the
+//                    epilogue;
+//   8 epilogue warps two per tensor-memory lane quarter, each on half of
+//                    the columns: drain tensor memory after each tile
+//                    (tcgen05.ld) and accumulate.
 // MMA operand A (M = 128 rows): X slices, two slices per 128-row block when
 // P <= 64 ("stacked"), one slice per block when 64 < P <= 128.  Operand B
 // (N rows): the six Y slices stacked, Qp rows each.  Accumulator column
@@ -57,16 +65,30 @@ namespace split {
 constexpr int KSTEP = 16;           // rows per MMA (16-bit inputs: K = 16)
 constexpr int TILE_STEPS = 16;      // steps per exact accumulation tile (256 rows)
 constexpr int NSLICE = 6;           // 8-bit slices per input
-constexpr int NDIG = 2;             // digit stages (converters -> MMA)
-constexpr int NST_MAX = 8;          // FP64 staging stages (cp.async ring, per thread)
-constexpr int NEXP = 4;             // exponent snapshot ring (converters -> epilogue)
-constexpr int MAX_CONV_WARPS = 16;  // converters: a per-shape multiple of 32 threads
-constexpr int NCONV_MAX = MAX_CONV_WARPS * 32;
-constexpr int NEPI_WARPS = 4;
-constexpr int NTHREADS_MAX = (MAX_CONV_WARPS + 1 + NEPI_WARPS) * 32;  // 672
+constexpr int NDIG_MAX = 6;         // digit stages (converters -> MMA): as many as fit, up to this
+constexpr int NEXP = 4;             // exponent snapshot ring (MMA warp -> epilogue)
+constexpr int MAX_MMAS = 9;         // MMAs per step (six slices of X against the Y slices, N <= 256 each)
+constexpr int NEPI_WARPS = 8;
 constexpr int TMEM_COLS = 512;
 constexpr int E_NONE = -4000;       // running exponent before any nonzero value
 constexpr long long kDefaultTimeout = 4000000000ll;  // SM cycles (~2 s)
+
+// Converter configurations: PER units per thread, DEPTH steps of loads in
+// flight ahead of the step being converted (DEPTH + 1 register sets).
+template <int PER>
+struct Conv;
+template <>
+struct Conv<1> {
+    static constexpr int MAX_THREADS = 512, DEPTH = 2;
+};
+template <>
+struct Conv<2> {
+    static constexpr int MAX_THREADS = 416, DEPTH = 1;
+};
+template <int PER>
+constexpr int block_threads() {
+    return Conv<PER>::MAX_THREADS + (1 + NEPI_WARPS) * 32;
+}
 
 struct Params {
     const double* X;
@@ -80,7 +102,7 @@ struct Params {
     int64_t steps_per_kr;
     int stacked;  // P <= 64
     int Qp;       // padded chunk width (multiple of 16)
-    int nconv;    // converter threads (multiple of 32, <= NCONV_MAX); MMA warp and 4 epilogue warps follow
+    int nconv;    // converter threads (multiple of 32); the MMA warp and the epilogue warps follow
     double* ws;     // [n_kr][P][Q]
     double* flush;  // [CTA][Qp][128]: binary64 totals of the epilogue lanes
     int* err;
@@ -107,15 +129,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: false (and the error word set) if the phase did not complete
-// within `timeout` SM cycles.
+// Bounded wait: false if the phase did not complete within `timeout` SM
+// cycles (the error word is then set to `code`), or if another warp raised
+// the CTA's abort flag meanwhile (`abort_flag` may be null: wait regardless).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long timeout, int* err,
-                                          int code) {
+                                          int code, const volatile int* abort_flag) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     unsigned ns = 16;  // back off so waiting warps leave issue slots to working ones
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (abort_flag && *abort_flag) return false;
         if (clock64() - t0 > timeout) {
             atomicCAS(err, 0, code);
             return false;
@@ -135,9 +159,6 @@ __device__ __forceinline__ void tc_fence_before() {
 }
 __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void named_sync(int id, int count) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 // Shared-memory matrix descriptor, no swizzle, K-major canonical layout:
@@ -171,89 +192,72 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
         : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// One lane of a converged warp (the same lane every time: the lowest).
+__device__ __forceinline__ bool elect_one() {
+    uint32_t pred = 0;
+    asm volatile("{\n.reg .pred P;\nelect.sync _|P, 0xffffffff;\nselp.u32 %0, 1, 0, P;\n}\n" : "=r"(pred));
+    return pred != 0;
+}
 
 // ------------------------------------------------------------ shared layout
 
 struct Layout {
     int nrb;            // 128-row blocks of operand A per step
     int units;          // (column, 4-row group) units per step: 4 * (P + Qw)
-    int nst;            // FP64 staging stages
+    int ndig;           // digit stages
+    int ne;             // exponent entries: P + Qp
     uint32_t a_bytes;   // operand A bytes per step
     uint32_t b_bytes;   // operand B bytes per step
     uint32_t stage;     // digit stage bytes (1024-aligned)
     uint32_t dig_off;   // offset of digit stage 0
-    uint32_t acc_off;   // binary64 accumulators [Qp][128]
-    uint32_t exp_off;   // running exponents [P + Qp] then snapshots [NEXP][P + Qp]
+    uint32_t acc_off;   // 64-bit integer accumulators [Qp][128]
+    uint32_t exps_off;  // per-stage column exponents [ndig][ne]
+    uint32_t snap_off;  // per-tile exponent snapshots [NEXP][ne]
     uint32_t misc_off;  // barriers, flags, tmem slot
-    uint32_t stg_off;   // FP64 staging ring: nst x [4 rows][units] doubles
-    uint32_t stg_bytes; // bytes per staging stage
     uint32_t total;
 };
 
 constexpr uint32_t kSmemBudget = 227u * 1024u;
+constexpr uint32_t kMiscBytes = 256u;
 
 __host__ __device__ inline Layout make_layout(int P, int Qp, int Qw, int stacked) {
     Layout L;
     L.nrb = stacked ? 3 : 6;
     L.units = 4 * (P + Qw);
+    L.ne = P + Qp;
     L.a_bytes = (uint32_t)L.nrb * 4096u;
     L.b_bytes = (uint32_t)NSLICE * Qp * 32u;
     L.stage = ((L.a_bytes + L.b_bytes) + 1023u) & ~1023u;
+    const uint32_t acc = (uint32_t)Qp * 128u * 8u;
+    const uint32_t exps = (uint32_t)L.ne * 4u;
+    const uint32_t fixed = acc + NEXP * exps + kMiscBytes + 256u;  // + alignment slack
+    int ndig = kSmemBudget > fixed ? (int)((kSmemBudget - fixed) / (L.stage + exps)) : 0;
+    if (ndig > NDIG_MAX) ndig = NDIG_MAX;
+    L.ndig = ndig;  // the host rejects fewer than 2
     L.dig_off = 0;
-    L.acc_off = L.dig_off + NDIG * L.stage;
-    const uint32_t ne = (uint32_t)(P + Qp);
-    L.exp_off = L.acc_off + (uint32_t)Qp * 128u * 8u;
-    L.misc_off = (L.exp_off + (1u + NEXP) * ne * 4u + 127u) & ~127u;
-    L.stg_off = (L.misc_off + 512u + 127u) & ~127u;
-    L.stg_bytes = (uint32_t)L.units * 32u;
-    // as many staging stages as fit (at least 2), up to NST_MAX
-    int nst = 2;
-    const int opts[4] = {8, 6, 4, 3};
-    for (int i = 0; i < 4; ++i)
-        if (L.stg_off + (uint32_t)opts[i] * L.stg_bytes <= kSmemBudget) {
-            nst = opts[i];
-            break;
-        }
-    L.nst = nst;
-    L.total = L.stg_off + (uint32_t)nst * L.stg_bytes;
+    L.acc_off = L.dig_off + (uint32_t)ndig * L.stage;
+    L.exps_off = L.acc_off + acc;
+    L.snap_off = L.exps_off + (uint32_t)ndig * exps;
+    L.misc_off = (L.snap_off + NEXP * exps + 127u) & ~127u;
+    L.total = L.misc_off + kMiscBytes;
     if (L.total < 120u * 1024u) L.total = 120u * 1024u;  // one CTA per SM (tensor memory is taken whole)
     return L;
 }
 
-__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, bool valid) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(valid ? 8 : 0)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// Waits until at most `pending` of this thread's groups are in flight.
-__device__ __forceinline__ void cp_async_wait(int pending) {
-    switch (pending) {
-        case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
-        case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
-        case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
-        case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
-        case 4: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
-        case 5: asm volatile("cp.async.wait_group 5;" ::: "memory"); break;
-        case 6: asm volatile("cp.async.wait_group 6;" ::: "memory"); break;
-        default: asm volatile("cp.async.wait_group 7;" ::: "memory"); break;
-    }
-}
-
 // misc area: byte offsets of the barriers and flags
 enum {
-    M_DIG_FULL = 0,     // NDIG x 8
-    M_DIG_EMPTY = 32,   // NDIG x 8
-    M_EXP_EMPTY = 64,   // NEXP x 8
-    M_TILE_FULL = 96,
-    M_TMEM_EMPTY = 104,
-    M_MMA_DONE = 112,
-    M_TMEM_SLOT = 128,
-    M_META = 136,       // NDIG ints: bit0 new tile, bits 1..: exponent slot
-    M_BRK = 160,        // 2 ints
-    M_ABORT = 168,
-    M_TILE_INFO = 172,  // slot | last << 8
-    M_CONV_FAIL = 176,
+    M_DIG_FULL = 0,     // NDIG_MAX x 8
+    M_DIG_EMPTY = 48,   // NDIG_MAX x 8
+    M_EXP_EMPTY = 96,   // NEXP x 8
+    M_TILE_FULL = 128,
+    M_TMEM_EMPTY = 136,
+    M_MMA_DONE = 144,
+    M_TMEM_SLOT = 152,
+    M_CHG = 160,        // NDIG_MAX ints: last step whose conversion grew a column exponent
+    M_ABORT = 184,
+    M_TILE_INFO = 188,  // slot | last << 8 | empty << 9 | exponents changed << 10
 };
+static_assert(M_TILE_INFO + 4 <= (int)kMiscBytes, "misc area");
 
 // ------------------------------------------------------------ digit maths
 
@@ -315,7 +319,9 @@ __device__ __forceinline__ uint32_t kmajor_off(int r, int g) {
 
 // ------------------------------------------------------------ the kernel
 
-__global__ void __launch_bounds__(NTHREADS_MAX, 1) k_split(const Params prm) {
+template <int PER>
+__global__ void __launch_bounds__(block_threads<PER>(), 1) k_split(const Params prm) {
+    constexpr int DEPTH = Conv<PER>::DEPTH;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int P = prm.P;
     const int kr = blockIdx.x / prm.n_qc, qc = blockIdx.x - kr * prm.n_qc;
@@ -324,21 +330,18 @@ __global__ void __launch_bounds__(NTHREADS_MAX, 1) k_split(const Params prm) {
     const int q0 = qc ? prm.q0[1] : prm.q0[0];
     const int Qw = qc ? prm.qw[1] : prm.qw[0];
     const int Qp = prm.Qp;
-    const double* __restrict__ Xg = prm.X;
-    const double* __restrict__ Yg = prm.Y;
-    const int64_t ldx = prm.ldx, ldy = prm.ldy, Ktot = prm.K;
+    const int64_t Ktot = prm.K;
     const int stacked = prm.stacked;
     const Layout L = make_layout(P, Qp, Qw, stacked);
-    const int NE = P + Qp;
+    const int NE = L.ne, ndig = L.ndig;
     unsigned char* dig = smem + L.dig_off;
-    double* acc = reinterpret_cast<double*>(smem + L.acc_off);  // epilogue integer sums (64-bit)
-    int* e_run = reinterpret_cast<int*>(smem + L.exp_off);
-    int* e_snap = e_run + NE;
+    long long* iacc = reinterpret_cast<long long*>(smem + L.acc_off);
+    int* exps = reinterpret_cast<int*>(smem + L.exps_off);
+    int* snap = reinterpret_cast<int*>(smem + L.snap_off);
     unsigned char* misc = smem + L.misc_off;
     const uint32_t misc_a = smem_addr(misc);
     auto bar = [&](int off) { return misc_a + (uint32_t)off; };
-    volatile int* meta = reinterpret_cast<volatile int*>(misc + M_META);
-    volatile int* brk = reinterpret_cast<volatile int*>(misc + M_BRK);
+    volatile int* chg_step = reinterpret_cast<volatile int*>(misc + M_CHG);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(misc + M_ABORT);
     volatile int* tile_info = reinterpret_cast<volatile int*>(misc + M_TILE_INFO);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -348,27 +351,26 @@ __global__ void __launch_bounds__(NTHREADS_MAX, 1) k_split(const Params prm) {
     const int NTHREADS = blockDim.x;
 
     // K range of this CTA, in 16-row steps
-    const int64_t steps_total = (prm.K + KSTEP - 1) / KSTEP;
+    const int64_t steps_total = (Ktot + KSTEP - 1) / KSTEP;
     const int64_t s_begin = (int64_t)kr * prm.steps_per_kr;
     int64_t s_end = s_begin + prm.steps_per_kr;
     if (s_end > steps_total) s_end = steps_total;
     const int64_t nsteps = s_end > s_begin ? s_end - s_begin : 0;
 
-    // ---- set-up: zero digit stages, accumulators, exponents; init barriers
-    for (uint32_t i = threadIdx.x * 16u; i < L.misc_off; i += NTHREADS * 16u)  // not the staging ring
+    // ---- set-up: zero everything up to the barriers; init barriers
+    for (uint32_t i = threadIdx.x * 16u; i < L.misc_off + kMiscBytes; i += NTHREADS * 16u)
         *reinterpret_cast<uint4*>(smem + i) = make_uint4(0, 0, 0, 0);
     __syncthreads();
-    for (int i = threadIdx.x; i < NE; i += NTHREADS) e_run[i] = E_NONE;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < NDIG; ++i) {
+        for (int i = 0; i < ndig; ++i) {
             mbar_init(bar(M_DIG_FULL + 8 * i), NCONV_WARPS);
             mbar_init(bar(M_DIG_EMPTY + 8 * i), 1);
+            chg_step[i] = -1;
         }
         for (int i = 0; i < NEXP; ++i) mbar_init(bar(M_EXP_EMPTY + 8 * i), NEPI_WARPS);
         mbar_init(bar(M_TILE_FULL), 1);
         mbar_init(bar(M_TMEM_EMPTY), NEPI_WARPS);
         mbar_init(bar(M_MMA_DONE), 1);
-        brk[0] = brk[1] = 0;
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -386,212 +388,235 @@ __global__ void __launch_bounds__(NTHREADS_MAX, 1) k_split(const Params prm) {
 
     if (warp < NCONV_WARPS) {
         // ================================================= converters
-        const int ct = threadIdx.x;  // 0..255
+        // Unit u = threadIdx.x + i * NCONV (i < PER) of every step: column
+        // c = u / 4 (X columns first, then this chunk's Y columns), rows
+        // 4 (u % 4) .. 4 (u % 4) + 3 of the step, i.e. k-group g = (u / 2) % 2
+        // of the K-major core rows, byte offset 8 (u % 2) inside them.  The
+        // four units of a column sit in adjacent lanes.
+        const int ct = threadIdx.x;
         const int units = L.units;
-        const int per = (units + NCONV - 1) / NCONV;  // <= 2 by the host's choice of NCONV
-        const int nst = L.nst;
-        const uint32_t stg_a = smem_addr(smem + L.stg_off);
-        double cur[2][4];
-        // unit u: column c = u / 4, rows 8g + 4h .. 8g + 4h + 3 of the step
-        // with g = (u / 2) % 2, h = u % 2.  Stage element (row r of 4, unit
-        // u) of ring slot `slot` sits at stg_off + slot * stg_bytes +
-        // (r * units + u) * 8: a thread reads back exactly what it copied, so
-        // no barrier guards the ring
-        auto issue_step = [&](int64_t s) {
-            if (s < nsteps) {
-                const int64_t row0 = (s_begin + s) * KSTEP;
-                const uint32_t base = stg_a + (uint32_t)(s % nst) * L.stg_bytes;
+        bool valid[PER];
+        const char* src[PER];   // column base
+        int64_t ldb[PER];       // row stride in bytes
+        int rq[PER];            // first row of the unit within a step
+        uint32_t off0[PER], dsl[PER];  // stage offset of slice 0 and the per-slice stride
+        int e[PER];
+        bool owner[PER];
 #pragma unroll
-                for (int it = 0; it < 2; ++it) {
-                    const int u = ct + it * NCONV;
-                    if (!(it < per && u < units)) continue;
-                    const int c = u >> 2, rb = (u & 3) * 4;
-                    const double* col;
-                    int64_t ld;
-                    if (c < P) {
-                        col = Xg + c;
-                        ld = ldx;
-                    } else {
-                        col = Yg + q0 + (c - P);
-                        ld = ldy;
-                    }
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const int64_t k = row0 + rb + r;
-                        const bool ok = k < Ktot;
-                        cp_async8(base + (uint32_t)((r * units + u) * 8), col + (ok ? k : 0) * ld, ok);
-                    }
-                }
+        for (int i = 0; i < PER; ++i) {
+            const int u = ct + i * NCONV;
+            valid[i] = u < units;
+            const int c = valid[i] ? u >> 2 : 0, g = (u >> 1) & 1, hb = (u & 1) * 8;
+            rq[i] = (u & 3) * 4;
+            owner[i] = valid[i] && (u & 3) == 0;
+            e[i] = E_NONE;
+            if (c < P) {
+                src[i] = reinterpret_cast<const char*>(prm.X + c);
+                ldb[i] = prm.ldx * 8;
+                // slice s in operand-A block (stacked ? s / 2 : s), row (stacked ? (s % 2) * 64 : 0) + c
+                off0[i] = kmajor_off(c, g) + hb;
+                dsl[i] = stacked ? 2048u : 4096u;
+            } else {
+                src[i] = reinterpret_cast<const char*>(prm.Y + q0 + (c - P));
+                ldb[i] = prm.ldy * 8;
+                off0[i] = L.a_bytes + kmajor_off(c - P, g) + hb;
+                dsl[i] = (uint32_t)Qp * 32u;
             }
-            cp_async_commit();  // one group per step, empty or not
-        };
-        auto read_step = [&](int64_t s) {
-            const double* base = reinterpret_cast<const double*>(smem + L.stg_off + (uint32_t)(s % nst) * L.stg_bytes);
+        }
+        // loads of step s (zero beyond this CTA's steps and beyond row K)
+        auto load_step = [&](double(&v)[PER][4], int64_t s) {
 #pragma unroll
-            for (int it = 0; it < 2; ++it) {
-                const int u = ct + it * NCONV;
-                const bool valid = it < per && u < units;
+            for (int i = 0; i < PER; ++i) {
+                const int64_t k = (s_begin + s) * KSTEP + rq[i];
+                const bool live = valid[i] && s < nsteps;
+                const int64_t left = live ? Ktot - k : 0;
+                const char* p = src[i] + (live ? k : 0) * ldb[i];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) cur[it][r] = valid ? base[r * units + u] : 0.0;
+                for (int r = 0; r < 4; ++r)
+                    v[i][r] = left > r ? __ldg(reinterpret_cast<const double*>(p + r * ldb[i])) : 0.0;
             }
         };
-        for (int i = 0; i < nst - 1; ++i) issue_step(i);
-        int64_t tile = -1;
-        int steps_in_tile = TILE_STEPS;
-        int slot = 0;
-        for (int64_t s = 0; s < nsteps; ++s) {
-            issue_step(s + nst - 1);
-            cp_async_wait(nst - 1);
-            read_step(s);
-            // -- phase 1: column exponents of this step, running maxima
-            if (ct == 0) brk[(s + 1) & 1] = 0;  // read by everyone before the previous barrier
+        int d = 0;
+        uint32_t phase = 0;
+        // converts step s from registers into digit stage d; false: stop
+        auto convert_step = [&](const double(&v)[PER][4], int64_t s) -> bool {
+            // -- running column exponents (registers; the four lanes of a column agree)
+            bool grew = false;
 #pragma unroll
-            for (int it = 0; it < 2; ++it) {
+            for (int i = 0; i < PER; ++i) {
                 uint32_t hm = 0;
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
-                    hm = max(hm, (uint32_t)((unsigned long long)__double_as_longlong(cur[it][r]) >> 32) & 0x7FFFFFFFu);
-                hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, 1));  // the four units of a column
-                hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, 2));  // are adjacent lanes
+                    hm = max(hm, (uint32_t)((unsigned long long)__double_as_longlong(v[i][r]) >> 32) & 0x7FFFFFFFu);
+                hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, 1));
+                hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, 2));
                 const int em = exp_from_hi(hm);
-                const int u = ct + it * NCONV;
-                if (it < per && u < units && (u & 3) == 0) {
-                    const int c = u >> 2;
-                    if (em > e_run[c]) {
-                        e_run[c] = em;
-                        brk[s & 1] = 1;
-                    }
+                if (valid[i] && em > e[i]) {
+                    e[i] = em;
+                    grew = true;
                 }
             }
-            named_sync(1, NCONV);
-            if (*abort_flag) break;  // uniform: set before this barrier by a failed warp
-            const bool expchg = brk[s & 1] != 0;  // a column exponent grew: new scale
-            const bool new_tile = expchg || steps_in_tile >= TILE_STEPS;
-            // waits are taken by lane 0 and broadcast, so failure is warp-uniform
-            bool ok = true;
-            if (new_tile) {
-                ++tile;
-                steps_in_tile = 0;
-                slot = (int)(tile % NEXP);
-                int w_ok = 1;
-                if (lane == 0)
-                    w_ok = mbar_wait(bar(M_EXP_EMPTY + 8 * slot), (uint32_t)(((tile / NEXP) & 1) ^ 1), tmo,
-                                     prm.err, 1);
-                ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
-                if (ok)
-                    for (int i = ct; i < NE; i += NCONV) e_snap[slot * NE + i] = e_run[i];
+            grew = __any_sync(0xffffffffu, grew);
+            // -- the stage must be free (waited by lane 0, broadcast: warp-uniform)
+            int w_ok = 1;
+            if (lane == 0)
+                w_ok = mbar_wait(bar(M_DIG_EMPTY + 8 * d), phase ^ 1u, tmo, prm.err, 2, abort_flag);
+            if (!__shfl_sync(0xffffffffu, w_ok, 0)) {
+                *abort_flag = 1;
+                return false;
             }
-            ++steps_in_tile;
-            const int d = (int)(s % NDIG);
-            if (ok) {
-                int w_ok = 1;
-                if (lane == 0)
-                    w_ok = mbar_wait(bar(M_DIG_EMPTY + 8 * d), (uint32_t)(((s / NDIG) & 1) ^ 1), tmo, prm.err, 2);
-                ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
-            }
-            if (!ok) {
-                *abort_flag = 1;  // the others stop at the next barrier
-                continue;
-            }
-            // -- phase 2: six fp16 slices of every value into the digit stage
+            if (grew && lane == 0) chg_step[d] = (int)s;
+            int* ex = exps + d * NE;
             unsigned char* stage = dig + d * L.stage;
 #pragma unroll
-            for (int it = 0; it < 2; ++it) {
-                const int u = ct + it * NCONV;
-                if (!(it < per && u < units)) continue;
-                const int c = u >> 2, g = (u >> 1) & 1, hb = (u & 1) * 8;
-                const int e = e_run[c];
+            for (int i = 0; i < PER; ++i) {
+                if (!valid[i]) continue;
+                if (owner[i]) ex[(ct + i * NCONV) >> 2] = e[i];
                 uint32_t w[NSLICE][2];
 #pragma unroll
                 for (int r = 0; r < 4; r += 2) {
                     uint32_t wp[NSLICE];
-                    split_pair(cur[it][r], cur[it][r + 1], e, wp);
+                    split_pair(v[i][r], v[i][r + 1], e[i], wp);
 #pragma unroll
                     for (int sl = 0; sl < NSLICE; ++sl) w[sl][r >> 1] = wp[sl];
                 }
-                if (c < P) {
-                    // operand A: slice sl in block (stacked ? sl/2 : sl), row (stacked ? (sl&1)*64 : 0) + c
 #pragma unroll
-                    for (int sl = 0; sl < NSLICE; ++sl) {
-                        const int blk = stacked ? (sl >> 1) : sl;
-                        const int row = (stacked ? (sl & 1) * 64 : 0) + c;
-                        *reinterpret_cast<uint2*>(stage + blk * 4096 + kmajor_off(row, g) + hb) =
-                            make_uint2(w[sl][0], w[sl][1]);
-                    }
-                } else {
-                    const int q = c - P;
-#pragma unroll
-                    for (int sl = 0; sl < NSLICE; ++sl)
-                        *reinterpret_cast<uint2*>(stage + L.a_bytes + kmajor_off(sl * Qp + q, g) + hb) =
-                            make_uint2(w[sl][0], w[sl][1]);
-                }
+                for (int sl = 0; sl < NSLICE; ++sl)
+                    *reinterpret_cast<uint2*>(stage + off0[i] + sl * dsl[i]) = make_uint2(w[sl][0], w[sl][1]);
             }
-            if (ct == 0) meta[d] = (new_tile ? 1 : 0) | (expchg ? 2 : 0) | (slot << 2);
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(bar(M_DIG_FULL + 8 * d));
+            if (++d == ndig) {
+                d = 0;
+                phase ^= 1u;
+            }
+            return true;
+        };
+        // DEPTH + 1 register sets in rotation: while step s is converted,
+        // the loads of steps s + 1 .. s + DEPTH are in flight
+        double buf[DEPTH + 1][PER][4];
+#pragma unroll
+        for (int j = 0; j < DEPTH; ++j) load_step(buf[j], j);
+        bool alive = true;
+        for (int64_t s0 = 0; s0 < nsteps && alive; s0 += DEPTH + 1) {
+#pragma unroll
+            for (int j = 0; j <= DEPTH; ++j) {
+                const int64_t s = s0 + j;
+                if (alive && s < nsteps) {
+                    load_step(buf[(j + DEPTH) % (DEPTH + 1)], s + DEPTH);
+                    alive = convert_step(buf[j], s) && !*abort_flag;
+                }
+            }
         }
-        cp_async_wait(0);  // no copy may land after the CTA exits
     } else if (warp == MMA_WARP) {
         // ================================================= MMA issuer
-        if (lane == 0) {
-            int64_t tile = -1;
-            int cur_slot = 0, cur_chg = 0;
-            bool failed = false;
-            uint32_t mma_phase = 0;
-            const uint32_t dig_a = smem_addr(dig);
-            for (int64_t s = 0; s < nsteps && !failed; ++s) {
-                const int d = (int)(s % NDIG);
-                if (!mbar_wait(bar(M_DIG_FULL + 8 * d), (uint32_t)((s / NDIG) & 1), tmo, prm.err, 3)) {
-                    failed = true;
-                    break;
+        // The warp runs the loop; waits are taken by lane 0 and broadcast,
+        // tcgen05 operations are issued by one elected lane.  The MMAs of a
+        // step are the same for every step up to the stage base address, so
+        // their descriptors are built once, in registers (issuing them from
+        // a per-MMA computation costs several times the MMA itself).
+        int64_t tile = -1;
+        int steps_in_tile = 0, cur_slot = 0, cur_chg = 0;
+        bool failed = false;
+        uint32_t mma_phase = 0, phase = 0;
+        int d = 0;
+        const uint32_t dig_a = smem_addr(dig);
+        uint64_t adesc[MAX_MMAS], bdesc[MAX_MMAS];
+        uint32_t dtm[MAX_MMAS], idesc[MAX_MMAS];
+        uint32_t first_mask = 0;  // MMAs of row block 0: they start a tile's accumulators
+        int nmma = 0;
+        {
+            const int maxs = 256 / Qp;  // slices per MMA (N <= 256)
+            int rb = 0, t0 = 0;
+#pragma unroll
+            for (int j = 0; j < MAX_MMAS; ++j) {
+                const int s_a = stacked ? 2 * rb : rb;  // first slice index of this row block
+                const int nt = NSLICE - s_a;            // slices t with s_a + t <= 5
+                const bool live = rb < L.nrb;
+                const int cnt = min(maxs, nt - t0);
+                adesc[j] = smem_desc(dig_a + (uint32_t)rb * 4096u, 128, 256);
+                bdesc[j] = smem_desc(dig_a + L.a_bytes + (uint32_t)(t0 * Qp * 32), 128, 256);
+                dtm[j] = tmem + (uint32_t)((s_a + t0) * Qp);
+                idesc[j] = instr_desc(live ? cnt * Qp : 16);
+                if (live && rb == 0) first_mask |= 1u << j;
+                nmma += live ? 1 : 0;
+                t0 += maxs;
+                if (t0 >= nt) {
+                    ++rb;
+                    t0 = 0;
                 }
-                tc_fence_after();
-                const int m = meta[d];
-                const bool new_tile = (m & 1) != 0;
-                if (new_tile) {
-                    if (tile >= 0) {
-                        // hand the finished tile to the epilogue
-                        mma_commit(bar(M_MMA_DONE));
-                        if (!mbar_wait(bar(M_MMA_DONE), mma_phase, tmo, prm.err, 4)) {
-                            failed = true;
-                            break;
-                        }
-                        mma_phase ^= 1;
+            }
+        }
+        auto lane0_wait = [&](uint32_t b, uint32_t par, int code) {
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(b, par, tmo, prm.err, code, abort_flag);
+            return __shfl_sync(0xffffffffu, ok, 0) != 0;
+        };
+        for (int64_t s = 0; s < nsteps; ++s) {
+            if (!lane0_wait(bar(M_DIG_FULL + 8 * d), phase, 3)) {
+                failed = true;
+                break;
+            }
+            tc_fence_after();
+            const bool chg = chg_step[d] == (int)s;
+            const bool new_tile = tile < 0 || chg || steps_in_tile >= TILE_STEPS;
+            if (new_tile) {
+                if (tile >= 0) {
+                    // hand the finished tile to the epilogue
+                    if (elect_one()) mma_commit(bar(M_MMA_DONE));
+                    __syncwarp();
+                    if (!lane0_wait(bar(M_MMA_DONE), mma_phase, 4)) {
+                        failed = true;
+                        break;
+                    }
+                    mma_phase ^= 1;
+                    if (lane == 0) {
                         *tile_info = cur_slot | (cur_chg << 10);
                         tc_fence_before();
                         mbar_arrive(bar(M_TILE_FULL));
-                        if (!mbar_wait(bar(M_TMEM_EMPTY), (uint32_t)(tile & 1), tmo, prm.err, 5)) {
-                            failed = true;
-                            break;
-                        }
-                        tc_fence_after();
                     }
-                    ++tile;
-                    cur_slot = m >> 2;
-                    cur_chg = (m >> 1) & 1;
-                }
-                const uint32_t sa = dig_a + (uint32_t)d * L.stage;
-                const uint32_t sb = sa + L.a_bytes;
-                const int maxs = 256 / Qp;  // slices per MMA (N <= 256)
-                // first MMA per accumulator block overwrites when the tile starts:
-                // row block 0 covers every block j = 0..5, so it goes first.
-                for (int rb = 0; rb < L.nrb; ++rb) {
-                    const int s_a = stacked ? 2 * rb : rb;  // first slice index of this row block
-                    const int nt = NSLICE - s_a;            // slices t with s_a + t <= 5
-                    for (int t0 = 0; t0 < nt; t0 += maxs) {
-                        const int cnt = min(maxs, nt - t0);
-                        const uint64_t ad = smem_desc(sa + rb * 4096, 128, 256);
-                        const uint64_t bd = smem_desc(sb + (uint32_t)(t0 * Qp * 32), 128, 256);
-                        const uint32_t dcol = (uint32_t)((s_a + t0) * Qp);
-                        mma_f16(tmem + dcol, ad, bd, instr_desc(cnt * Qp), (rb == 0 && new_tile) ? 0u : 1u);
+                    if (!lane0_wait(bar(M_TMEM_EMPTY), (uint32_t)(tile & 1), 5)) {
+                        failed = true;
+                        break;
                     }
+                    tc_fence_after();
                 }
+                ++tile;
+                steps_in_tile = 0;
+                cur_slot = (int)(tile % NEXP);
+                cur_chg = chg ? 1 : 0;
+                if (!lane0_wait(bar(M_EXP_EMPTY + 8 * cur_slot), (uint32_t)(((tile / NEXP) & 1) ^ 1), 8)) {
+                    failed = true;
+                    break;
+                }
+                const int* ex = exps + d * NE;
+                int* sn = snap + cur_slot * NE;
+                for (int i = lane; i < NE; i += 32) sn[i] = ex[i];
+                __syncwarp();
+            }
+            ++steps_in_tile;
+            // stage d's operands: the same descriptors moved by d stages (the
+            // address field counts 16-byte units and stays below 2^14)
+            const uint64_t so = (uint64_t)(((uint32_t)d * L.stage) >> 4);
+            const uint32_t keep = new_tile ? ~first_mask : ~0u;
+            if (elect_one()) {
+#pragma unroll
+                for (int j = 0; j < MAX_MMAS; ++j)
+                    if (j < nmma) mma_f16(dtm[j], adesc[j] + so, bdesc[j] + so, idesc[j], (keep >> j) & 1u);
                 mma_commit(bar(M_DIG_EMPTY + 8 * d));
             }
-            // last tile (or drain after a failure)
-            mma_commit(bar(M_MMA_DONE));
-            const bool drained = mbar_wait(bar(M_MMA_DONE), mma_phase, kDefaultTimeout, prm.err, 6);
+            __syncwarp();
+            if (++d == ndig) {
+                d = 0;
+                phase ^= 1u;
+            }
+        }
+        // last tile (or drain after a failure): no MMA may be in flight at exit
+        if (elect_one()) mma_commit(bar(M_MMA_DONE));
+        __syncwarp();
+        if (lane == 0) {
+            const bool drained = mbar_wait(bar(M_MMA_DONE), mma_phase, kDefaultTimeout, prm.err, 6, nullptr);
             if (!failed && drained && tile >= 0) {
                 *tile_info = cur_slot | (1 << 8) | (cur_chg << 10);
                 tc_fence_before();
@@ -599,6 +624,8 @@ __global__ void __launch_bounds__(NTHREADS_MAX, 1) k_split(const Params prm) {
             } else if (tile < 0 && !failed) {
                 *tile_info = 1 << 9;  // empty range: nothing to drain
                 mbar_arrive(bar(M_TILE_FULL));
+            } else {
+                *abort_flag = 1;  // the epilogue stops waiting
             }
         }
         __syncwarp();
@@ -608,16 +635,18 @@ __global__ void __launch_bounds__(NTHREADS_MAX, 1) k_split(const Params prm) {
         // shared memory, at the scale of the current column exponents.  It
         // moves to binary64 (`flush`, this thread's own entries in global
         // memory) only when an exponent grows, when the integer sum would
-        // overflow, and at the end -- not once per tile.
+        // overflow, and at the end -- not once per tile.  Warps w and w + 4
+        // share a lane quarter and split the columns.
         const int ew = warp - EPI_WARP0;
         const int lane_base = 32 * (warp & 3);
         const int row = lane_base + lane;  // TMEM lane = accumulator row
         const int p = stacked ? (row & 63) : row;
         const int half = stacked ? (row >> 6) : 0;
         const bool prow = p < P;
-        long long* iacc = reinterpret_cast<long long*>(acc);
+        const int qh = Qp / 2;  // a multiple of 8
+        const int qlo = (ew >> 2) * qh, qhi = qlo + qh;
         double* flush = prm.flush + (int64_t)blockIdx.x * Qp * 128;
-        for (int q = 0; q < Qp; ++q) flush[q * 128 + row] = 0.0;
+        for (int q = qlo; q < qhi; ++q) flush[q * 128 + row] = 0.0;
         auto scaled = [](long long a, int E) {
             return (E >= -1022 && E <= 1023) ? (double)a * __longlong_as_double((long long)(E + 1023) << 52)
                                              : scalbn((double)a, E);
@@ -625,7 +654,7 @@ __global__ void __launch_bounds__(NTHREADS_MAX, 1) k_split(const Params prm) {
         auto flush_all = [&](const int* exs) {
             if (!prow) return;
             const int epf = exs[p];
-            for (int q = 0; q < Qw; ++q) {
+            for (int q = qlo; q < min(qhi, Qw); ++q) {
                 const long long a = iacc[q * 128 + row];
                 if (a == 0) continue;
                 iacc[q * 128 + row] = 0;
@@ -634,20 +663,22 @@ __global__ void __launch_bounds__(NTHREADS_MAX, 1) k_split(const Params prm) {
         };
         int prev_slot = -1;
         for (int64_t tile = 0;; ++tile) {
-            if (!mbar_wait(bar(M_TILE_FULL), (uint32_t)(tile & 1), tmo, prm.err, 7)) break;
+            int w_ok = 1;
+            if (lane == 0) w_ok = mbar_wait(bar(M_TILE_FULL), (uint32_t)(tile & 1), tmo, prm.err, 7, abort_flag);
+            if (!__shfl_sync(0xffffffffu, w_ok, 0)) break;
             tc_fence_after();
             const int info = *tile_info;
             if (info & (1 << 9)) break;
             const int slot = info & 0xFF;
             const bool chg = (info >> 10) & 1;
             if (prev_slot >= 0) {
-                if (chg) flush_all(e_snap + prev_slot * NE);  // sums so far carry the old scale
+                if (chg) flush_all(snap + prev_slot * NE);  // sums so far carry the old scale
                 __syncwarp();
                 if (lane == 0) mbar_arrive(bar(M_EXP_EMPTY + 8 * prev_slot));
             }
-            const int* ex = e_snap + slot * NE;
+            const int* ex = snap + slot * NE;
             const int ep = prow ? ex[p] : 0;
-            for (int qb = 0; qb < Qp; qb += 8) {
+            for (int qb = qlo; qb < qhi; qb += 8) {
                 uint32_t v[NSLICE][8];
 #pragma unroll
                 for (int j = 0; j < NSLICE; ++j)
@@ -686,7 +717,6 @@ __global__ void __launch_bounds__(NTHREADS_MAX, 1) k_split(const Params prm) {
                 break;
             }
         }
-        (void)ew;
     }
 
     __syncthreads();
@@ -746,6 +776,17 @@ __global__ void k_split_combine(const double* ws, int n_kr, int P, int Q, int M,
 }
 
 long long g_timeout = kDefaultTimeout;
+
+// MMAs per step for a chunk width Qp: the kernel builds at most MAX_MMAS.
+int count_mmas(int stacked, int Qp) {
+    const int maxs = 256 / Qp;
+    int n = 0;
+    for (int rb = 0; rb < (stacked ? 3 : 6); ++rb) {
+        const int nt = NSLICE - (stacked ? 2 * rb : rb);
+        n += (nt + maxs - 1) / maxs;
+    }
+    return n;
+}
 
 }  // namespace split
 
@@ -825,22 +866,23 @@ extern "C" tsm_status tsm_tsmttsm_split(tsm_op opA, tsm_dtype dtype, int M, int 
     prm.flush = ws->partials + (size_t)n_kr * P * Q;
     prm.err = reinterpret_cast<int*>(ws->tickets) + 32;  // error word of this stream
     const split::Layout L = split::make_layout(P, prm.Qp, qmax, prm.stacked);
-    // converters: the fewest rounds of units, spread evenly over a multiple
-    // of 32 threads
-    {
-        const int units = L.units;
-        const int rounds = (units + split::NCONV_MAX - 1) / split::NCONV_MAX;
-        int nconv = (units + rounds - 1) / rounds;
-        nconv = (nconv + 31) & ~31;
-        if (nconv > split::NCONV_MAX) nconv = split::NCONV_MAX;
-        prm.nconv = nconv;
-    }
-    if (L.total > di.smem_optin) return TSM_ERR_NOT_SUPPORTED;
-    if (cudaFuncSetAttribute(split::k_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) !=
-        cudaSuccess)
+    if (L.ndig < 2 || L.total > di.smem_optin || split::count_mmas(prm.stacked, prm.Qp) > split::MAX_MMAS)
+        return TSM_ERR_NOT_SUPPORTED;
+    // converters: one unit per thread when the units fit one thread each
+    // (two steps of loads in flight), else two (one step in flight)
+    const int per = L.units <= split::Conv<1>::MAX_THREADS ? 1 : 2;
+    prm.nconv = (((L.units + per - 1) / per) + 31) & ~31;
+    if (prm.nconv > (per == 1 ? split::Conv<1>::MAX_THREADS : split::Conv<2>::MAX_THREADS))
+        return TSM_ERR_NOT_SUPPORTED;
+    const void* fn = per == 1 ? (const void*)split::k_split<1> : (const void*)split::k_split<2>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) != cudaSuccess)
         return TSM_ERR_LAUNCH;
     if (cudaMemsetAsync(prm.err, 0, sizeof(int), s) != cudaSuccess) return TSM_ERR_LAUNCH;
-    split::k_split<<<n_kr * prm.n_qc, prm.nconv + (1 + split::NEPI_WARPS) * 32, L.total, s>>>(prm);
+    const int threads = prm.nconv + (1 + split::NEPI_WARPS) * 32;
+    if (per == 1)
+        split::k_split<1><<<n_kr * prm.n_qc, threads, L.total, s>>>(prm);
+    else
+        split::k_split<2><<<n_kr * prm.n_qc, threads, L.total, s>>>(prm);
     if (cudaGetLastError() != cudaSuccess) return TSM_ERR_LAUNCH;
     const int outs = M * N;
     split::k_split_combine<<<(outs + 127) / 128, 128, 0, s>>>(
