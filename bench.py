@@ -246,6 +246,18 @@ def run_case(args):
     print(json.dumps({"case": args.case, "K": K, "ok": True}))
 
 
+def max_over_ranks(x, device=None):
+    """The largest of every rank's x: the job's time is its slowest rank's
+    (x itself when the process is not part of a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args, bw, bw_src):
     import torch
     import torch.distributed as dist
@@ -317,11 +329,7 @@ def run_ours(args, bw, bw_src):
                for cfg in SWEEP}
 
     ideal = {cfg: ideal_seconds(cfg[0], cfg[1], cfg[2], K, bw, p64) for cfg in SWEEP}
-    ms_step = total_ms / args.steps
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(total_ms / args.steps, dev)
     value = 100.0 * sum(ideal.values()) / (ms_step * 1e-3)
 
     sweep = []
