@@ -540,6 +540,74 @@ def run_tsmm_extra(flatA, flatB, K, bw, p64):
     return {"roofline_pct_whole_sweep": 100 * ideal / meas, "calls": out}
 
 
+GS_CASES = [(True, 32, 32), (True, 64, 64), (False, 64, 64), (False, 8, 8)]
+
+
+def run_gs_extra(flatA, flatB, K, bw, p64):
+    """Block Gram-Schmidt step (C = A^H B, B -= A C) through tsm_gs_step at
+    K = 2^24: time against the sum of the two products' roofline times (the
+    TSMM reads and writes B: beta = 1)."""
+    import torch
+    import paper_1905_03136_gb300 as tsm
+    out, ideal, meas = [], 0.0, 0.0
+    Bw = torch.empty(K * 128, dtype=torch.float64, device=flatA.device)
+    for (cplx, M, N) in GS_CASES:
+        c = 2 if cplx else 1
+        A = flatA[: K * M * c]
+        B = Bw[: K * N * c]
+        B.copy_(flatB[: K * N * c])
+        if cplx:
+            A, B = A.view(torch.complex128), B.view(torch.complex128)
+        A, B = A.view(K, M), B.view(K, N)
+        C = torch.empty((M, N), dtype=A.dtype, device=A.device)
+        ms = _time(lambda: tsm.gs_step(A, B, C), reps=2)
+        f1, b1 = model(cplx, M, N, K)
+        b2 = b1 + 8.0 * c * N * K  # TSMM with beta = 1 also reads B
+        t_ideal = max(b1 / (bw * 1e9), f1 / (p64 * 1e9)) + max(b2 / (bw * 1e9), f1 / (p64 * 1e9))
+        ideal += t_ideal
+        meas += ms * 1e-3
+        out.append({"dtype": "c64" if cplx else "r64", "M": M, "N": N, "ms": round(ms, 4),
+                    "roofline_pct": round(100 * t_ideal / (ms * 1e-3), 2)})
+    del Bw
+    torch.cuda.empty_cache()
+    return {"what": "tsm_gs_step: TSMTTSM (op C) then TSMM (alpha=-1, beta=1) on one stream, C on the device",
+            "roofline_pct_all": 100 * ideal / meas, "calls": out}
+
+
+RAMP_K = [10 ** 4, 3 * 10 ** 4, 10 ** 5, 3 * 10 ** 5, 10 ** 6, 1 << 21, 1 << 22, 1 << 24]
+RAMP_CASES = [(False, 4, 4), (False, 16, 16), (True, 8, 8), (True, 32, 32)]
+
+
+def run_ramp_extra(flatA, flatB, bw, p64):
+    """Small-K ramp (the paper's Fig. 18 experiment): percent of roofline of
+    the tuned TSMTTSM as K grows from 10^4 to 2^24.  `fixed_us` is the time
+    of a call with one 16-row slab per CTA (K = 16 x grid): launch, the
+    in-CTA and the cross-CTA reductions, and the epilogue, with almost no
+    streaming; `fixed_share` is that time over each call's time."""
+    import torch
+    import paper_1905_03136_gb300 as tsm
+    res = []
+    for (cplx, M, N) in RAMP_CASES:
+        dt = tsm.C64 if cplx else tsm.R64
+        C = torch.zeros((M, N), dtype=torch.complex128 if cplx else torch.float64, device=flatA.device)
+        var, grid = tsm.choose(tsm.KIND_TSMTTSM, dt, M, N, 1 << 20)
+        k0 = 16 * max(grid, 1)
+        A0, B0 = _views(flatA, flatB, cplx, M, N, k0)
+        fixed = _time(lambda: tsm.tsmttsm(A0, B0, C, op="C" if cplx else "T", variant=var, grid=grid), reps=20,
+                      warm=3)
+        pts = []
+        for K in RAMP_K:
+            A, B = _views(flatA, flatB, cplx, M, N, K)
+            reps = 20 if K <= (1 << 22) else 2
+            ms = _time(lambda: tsm.tsmttsm(A, B, C, op="C" if cplx else "T"), reps=reps, warm=2)
+            t_ideal = ideal_seconds(cplx, M, N, K, bw, p64)
+            pts.append({"K": K, "us": round(ms * 1e3, 2), "roofline_pct": round(100 * t_ideal / (ms * 1e-3), 2),
+                        "fixed_share": round(fixed / ms, 4)})
+        res.append({"dtype": "c64" if cplx else "r64", "M": M, "N": N, "grid_at_2^20": grid,
+                    "fixed_us": round(fixed * 1e3, 2), "points": pts})
+    return {"what": "TSMTTSM % of roofline vs K (tuned variant per K)", "cases": res}
+
+
 def batched_workload(seed=0, count=256):
     """The batched mixed workload: op TSMTTSM/TSMM and dtype 50/50, M, N
     uniform in [1, 64], K = floor(2^(16 + 6u)) (log-uniform in [2^16, 2^22])."""
@@ -637,8 +705,42 @@ def run_batched_extra(flatA, flatB):
     return res
 
 
+def run_cublas_extra(flatA, flatB, K, bw, p64):
+    """The same sweep through cuBLAS (torch.matmul on transposed views of the
+    same buffers: DGEMM with op T, ZGEMM with op C), for comparison with the
+    library's kernels; percent of the same roofline."""
+    import torch
+    rows = []
+    ideal_sum = meas_sum = 0.0
+    for cfg in SWEEP:
+        A, B = _views(flatA, flatB, cfg[0], cfg[1], cfg[2], K)
+        At = A.mH if cfg[0] else A.t()
+        out = torch.matmul(At, B)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record()
+        for _ in range(reps):
+            out = torch.matmul(At, B)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        ideal = ideal_seconds(cfg[0], cfg[1], cfg[2], K, bw, p64)
+        ideal_sum += ideal
+        meas_sum += ms * 1e-3
+        rows.append({"dtype": "c64" if cfg[0] else "r64", "M": cfg[1], "N": cfg[2], "ms": round(ms, 4),
+                     "roofline_pct": round(100.0 * ideal / (ms * 1e-3), 2)})
+        del out
+    return {"what": "cuBLAS DGEMM (op T) / ZGEMM (op C) via torch.matmul on the same buffers",
+            "value": 100.0 * ideal_sum / meas_sum, "unit": "% of roofline", "sweep": rows}
+
+
 def run_extras(args, flatA, flatB, K, bw, p64):
     ex = {}
+    try:
+        ex["cublas"] = run_cublas_extra(flatA, flatB, K, bw, p64)
+    except Exception as e:  # reported, never hidden
+        ex["cublas"] = {"error": repr(e)}
     try:
         ex["split"] = run_split_extra(flatA, flatB, K, bw)
     except Exception as e:  # reported, never hidden
@@ -647,6 +749,14 @@ def run_extras(args, flatA, flatB, K, bw, p64):
         ex["tsmm_sweep"] = run_tsmm_extra(flatA, flatB, K, bw, p64)
     except Exception as e:
         ex["tsmm_sweep"] = {"error": repr(e)}
+    try:
+        ex["gs_step"] = run_gs_extra(flatA, flatB, K, bw, p64)
+    except Exception as e:
+        ex["gs_step"] = {"error": repr(e)}
+    try:
+        ex["small_k_ramp"] = run_ramp_extra(flatA, flatB, bw, p64)
+    except Exception as e:
+        ex["small_k_ramp"] = {"error": repr(e)}
     try:
         ex["batched"] = run_batched_extra(flatA, flatB)
     except Exception as e:

@@ -158,6 +158,28 @@ tsm_status tsm_tsmm_ex(tsm_op opC, tsm_dtype dtype, int M, int N, int64_t K,
                        const void *C, int64_t ldc, const double *beta, void *B,
                        int64_t ldb, int variant, int grid, tsm_stream_t stream);
 
+/*
+ * One block Gram-Schmidt projection step, the use that motivates TSMTTSM
+ * and TSMM in the paper (Sec. 1.1): with A (K x M) holding orthonormal
+ * columns,
+ *     C = A^H B        (TSMTTSM, op C; A^T B for real data)
+ *     B = B - A C      (TSMM, alpha = -1, beta = 1)
+ * removes from B (K x N, in place) its components in span(A) and leaves
+ * the coefficients in C (M x N, ldc >= N), a caller-owned DEVICE buffer.
+ * C does not travel to the host between the two products: the TSMM kernel
+ * reads it from device memory once per CTA into shared memory.  Both
+ * products use the variants the tuning table selects; the two launches are
+ * enqueued on `stream` back to back (no host synchronisation, capturable in
+ * a CUDA graph).  With A not orthonormal the same two products run (one
+ * classical Gram-Schmidt projection).
+ * Errors: as tsm_tsmttsm / tsm_tsmm; C == NULL -> INVALID_VALUE; every check
+ * runs before the first launch, so on an error B and C are untouched.  C must
+ * not alias A or B.  K == 0 sets C to zero and leaves B unchanged.
+ */
+tsm_status tsm_gs_step(tsm_dtype dtype, int M, int N, int64_t K, const void *A,
+                       int64_t lda, void *B, int64_t ldb, void *C, int64_t ldc,
+                       tsm_stream_t stream);
+
 /* The variant index and grid the library would use for this shape
  * (tuning table first, then the built-in heuristic). */
 tsm_status tsm_choose(tsm_kind kind, tsm_dtype dtype, int M, int N, int64_t K,

@@ -15,7 +15,7 @@ from . import _lib
 from ._lib import (C64, KIND_TSMM, KIND_TSMTTSM, OP_C, OP_N, OP_T, R64, TsmError, VariantInfo,
                    TuneSample, call, load, raw, scalar)
 
-__all__ = ["tsmttsm", "tsmm", "fill_random", "variants", "choose", "tune", "time_variant",
+__all__ = ["tsmttsm", "tsmm", "gs_step", "fill_random", "variants", "choose", "tune", "time_variant",
            "TsmError", "load", "R64", "C64", "OP_T", "OP_C", "OP_N"]
 
 _OPS = {"T": OP_T, "C": OP_C, "N": OP_N, OP_T: OP_T, OP_C: OP_C, OP_N: OP_N}
@@ -85,6 +85,24 @@ def tsmm(A, Cm, B=None, alpha=1.0, beta=0.0, stream=None, variant=-1, grid=0):
          ctypes.c_void_p(Cm.data_ptr()), _ld(Cm, "C"), scalar(beta, cplx), ctypes.c_void_p(B.data_ptr()),
          _ld(B, "B"), int(variant), int(grid), _stream(stream))
     return B
+
+
+def gs_step(A, B, C=None, stream=None):
+    """One block Gram-Schmidt projection in place: C = A^H B, B -= A C.
+    Returns C (M x N, on the device)."""
+    torch = _torch()
+    dt = _dtype_code(A)
+    K, M = A.shape
+    N = B.shape[1]
+    if B.shape[0] != K or _dtype_code(B) != dt:
+        raise ValueError("A and B must have the same row count and dtype")
+    if C is None:
+        C = torch.empty((M, N), dtype=A.dtype, device=A.device)
+    elif C.shape != (M, N) or _dtype_code(C) != dt:
+        raise ValueError("C must be M x N with A's dtype")
+    call("tsm_gs_step", dt, M, N, K, ctypes.c_void_p(A.data_ptr()), _ld(A, "A"), ctypes.c_void_p(B.data_ptr()),
+         _ld(B, "B"), ctypes.c_void_p(C.data_ptr()), _ld(C, "C"), _stream(stream))
+    return C
 
 
 DIST = {"uniform": 0, "loguniform": 1, "smallint": 2, "ones": 3}

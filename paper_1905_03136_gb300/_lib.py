@@ -51,6 +51,7 @@ SIGNATURES = {
     "tsm_tsmm": (i32, [i32, i32, i32, i32, i64, dp, vp, i64, vp, i64, dp, vp, i64, vp]),
     "tsm_tsmttsm_ex": (i32, [i32, i32, i32, i32, i64, dp, vp, i64, vp, i64, dp, vp, i64, i32, i32, vp]),
     "tsm_tsmm_ex": (i32, [i32, i32, i32, i32, i64, dp, vp, i64, vp, i64, dp, vp, i64, i32, i32, vp]),
+    "tsm_gs_step": (i32, [i32, i32, i32, i64, vp, i64, vp, i64, vp, i64, vp]),
     "tsm_status_string": (ctypes.c_char_p, [i32]),
     "tsm_version": (ctypes.c_char_p, []),
     "tsm_release": (i32, []),

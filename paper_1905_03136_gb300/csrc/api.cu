@@ -386,6 +386,21 @@ tsm_status tsm_tsmm_ex(tsm_op opC, tsm_dtype dtype, int M, int N, int64_t K, con
                     (cudaStream_t)stream);
 }
 
+tsm_status tsm_gs_step(tsm_dtype dtype, int M, int N, int64_t K, const void* A, int64_t lda, void* B,
+                       int64_t ldb, void* C, int64_t ldc, tsm_stream_t stream) {
+    const double one[2] = {1.0, 0.0}, zero[2] = {0.0, 0.0}, minus_one[2] = {-1.0, 0.0};
+    // every argument is checked before the first launch, so that an error
+    // leaves B and C untouched
+    tsm_status st = validate_common(dtype, M, N, K, one, zero);
+    if (st != TSM_OK) return st;
+    if (lda < M || ldb < N || ldc < N || !C) return TSM_ERR_INVALID_VALUE;
+    if (K > 0 && (!A || !B)) return TSM_ERR_INVALID_VALUE;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = run_tsmttsm(TSM_OP_C, dtype, M, N, K, one, A, lda, B, ldb, zero, C, ldc, -1, 0, s)) != TSM_OK)
+        return st;
+    return run_tsmm(TSM_OP_N, dtype, M, N, K, minus_one, A, lda, C, ldc, one, B, ldb, -1, 0, s);
+}
+
 const char* tsm_status_string(tsm_status s) {
     switch (s) {
         case TSM_OK: return "success";
