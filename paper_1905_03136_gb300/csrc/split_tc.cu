@@ -203,7 +203,7 @@ __device__ __forceinline__ bool elect_one() {
 
 struct Layout {
     int nrb;            // 128-row blocks of operand A per step
-    int units;          // (column, 4-row group) units per step: 4 * (P + Qw)
+    int units;          // (column slot, 4-row group) units per step, a multiple of 32
     int ndig;           // digit stages
     int ne;             // exponent entries: P + Qp
     uint32_t a_bytes;   // operand A bytes per step
@@ -223,7 +223,7 @@ constexpr uint32_t kMiscBytes = 256u;
 __host__ __device__ inline Layout make_layout(int P, int Qp, int Qw, int stacked) {
     Layout L;
     L.nrb = stacked ? 3 : 6;
-    L.units = 4 * (P + Qw);
+    L.units = 32 * ((((P + 7) & ~7) + Qw + 7) / 8);  // 4 units per column slot, 8 slots per group of 32
     L.ne = P + Qp;
     L.a_bytes = (uint32_t)L.nrb * 4096u;
     L.b_bytes = (uint32_t)NSLICE * Qp * 32u;
@@ -282,26 +282,37 @@ __device__ __forceinline__ unsigned long long fixed47(double x, int e, uint32_t*
 // The six fp16 slices of two values a (row r) and b (row r + 1) of one
 // column, packed per slice as (a, b) in one 32-bit word, sign applied.  A
 // digit byte placed under the fp16 exponent of 1024 (0x64XX) is 1024 + byte
-// exactly; one packed subtraction removes 1024 (+ 128) from both halves.
+// exactly.  Byte permutes gather the digit bytes of both values two slices at
+// a time and place them under 0x64; one packed fused multiply-add then forms
+// sign * (1024 + byte) - sign * bias, bias = 1024 for the top digit and 1152
+// (1024 + 128) for the balanced low digits: exact, since every result is a
+// small integer.
 __device__ __forceinline__ void split_pair(double xa, double xb, int e, uint32_t* w) {
     uint32_t sa, sb;
     const unsigned long long ya = fixed47(xa, e, &sa), yb = fixed47(xb, e, &sb);
     const uint32_t alo = (uint32_t)ya, ahi = (uint32_t)(ya >> 32);
     const uint32_t blo = (uint32_t)yb, bhi = (uint32_t)(yb >> 32);
-    const uint32_t sg = (sa >> 16) | sb;
-    const __half2 top = __halves2half2(__ushort_as_half(0x6400), __ushort_as_half(0x6400));  // 1024
-    const __half2 low = __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480));  // 1152
-    auto make = [&](uint32_t x, uint32_t y, uint32_t sel, __half2 bias) {
-        uint32_t u = (__byte_perm(x, y, sel) & 0x00FF00FFu) | 0x64006400u;
-        __half2 h = __hsub2(*reinterpret_cast<__half2*>(&u), bias);
-        return *reinterpret_cast<uint32_t*>(&h) ^ sg;
+    const uint32_t sg = (sa >> 16) | sb;       // sign of a in bit 15, of b in bit 31
+    const uint32_t k64 = 0x64646464u;
+    const uint32_t mul = 0x3C003C00u | sg;     // (+-1.0, +-1.0)
+    const uint32_t c_top = 0xE400E400u ^ sg;   // -1024 * sign
+    const uint32_t c_low = 0xE480E480u ^ sg;   // -1152 * sign
+    // [b5 a5 b4 a4], [b3 a3 b2 a2], [b1 a1 b0 a0] (byte n of Y written an, bn)
+    const uint32_t m45 = __byte_perm(ahi, bhi, 0x5140);
+    const uint32_t m23 = __byte_perm(alo, blo, 0x7362);
+    const uint32_t m01 = __byte_perm(alo, blo, 0x5140);
+    auto fin = [&](uint32_t pair, uint32_t sel, uint32_t add) {
+        uint32_t u = __byte_perm(pair, k64, sel);  // [0x64 b 0x64 a]
+        __half2 h = __hfma2(*reinterpret_cast<__half2*>(&u), *reinterpret_cast<const __half2*>(&mul),
+                            *reinterpret_cast<const __half2*>(&add));
+        return *reinterpret_cast<uint32_t*>(&h);
     };
-    w[0] = make(ahi, bhi, 0x0501, top);  // byte 5
-    w[1] = make(ahi, bhi, 0x0400, low);  // byte 4
-    w[2] = make(alo, blo, 0x0703, low);  // byte 3
-    w[3] = make(alo, blo, 0x0602, low);  // byte 2
-    w[4] = make(alo, blo, 0x0501, low);  // byte 1
-    w[5] = make(alo, blo, 0x0400, low);  // byte 0
+    w[0] = fin(m45, 0x4342, c_top);  // byte 5
+    w[1] = fin(m45, 0x4140, c_low);  // byte 4
+    w[2] = fin(m23, 0x4342, c_low);  // byte 3
+    w[3] = fin(m23, 0x4140, c_low);  // byte 2
+    w[4] = fin(m01, 0x4342, c_low);  // byte 1
+    w[5] = fin(m01, 0x4140, c_low);  // byte 0
 }
 
 // Exponent from the largest magnitude high word of a column: |x| < 2^e for
@@ -388,38 +399,46 @@ __global__ void __launch_bounds__(block_threads<PER>(), 1) k_split(const Params 
 
     if (warp < NCONV_WARPS) {
         // ================================================= converters
-        // Unit u = threadIdx.x + i * NCONV (i < PER) of every step: column
-        // c = u / 4 (X columns first, then this chunk's Y columns), rows
-        // 4 (u % 4) .. 4 (u % 4) + 3 of the step, i.e. k-group g = (u / 2) % 2
-        // of the K-major core rows, byte offset 8 (u % 2) inside them.  The
-        // four units of a column sit in adjacent lanes.
+        // Unit u = threadIdx.x + i * NCONV (i < PER) of every step.  Each
+        // group of 32 units covers 8 column slots: slot c = 8 (u / 32) +
+        // (u / 2) % 8, k-group g = (u / 16) % 2 of the K-major core rows
+        // (rows 8g .. 8g + 7 of the step), byte offset 8 (u % 2) inside them
+        // (rows 8g + 4 (u % 2) .. + 3).  A half-warp thus stores one
+        // contiguous 128-byte core row (no bank conflicts), and the four
+        // units of a column are lanes l, l ^ 1, l ^ 16, l ^ 17.  Slots
+        // [0, P) are X's columns, [P8, P8 + Qw) this chunk's Y columns
+        // (P8 = P rounded up to 8, so Y starts on a group); the rest are idle.
         const int ct = threadIdx.x;
-        const int units = L.units;
+        const int P8 = (P + 7) & ~7;
         bool valid[PER];
         const char* src[PER];   // column base
         int64_t ldb[PER];       // row stride in bytes
         int rq[PER];            // first row of the unit within a step
         uint32_t off0[PER], dsl[PER];  // stage offset of slice 0 and the per-slice stride
         int e[PER];
+        int col[PER];           // exponent index: X columns, then Y columns
         bool owner[PER];
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
             const int u = ct + i * NCONV;
-            valid[i] = u < units;
-            const int c = valid[i] ? u >> 2 : 0, g = (u >> 1) & 1, hb = (u & 1) * 8;
-            rq[i] = (u & 3) * 4;
-            owner[i] = valid[i] && (u & 3) == 0;
+            const int slot = 8 * (u >> 5) + ((u >> 1) & 7), g = (u >> 4) & 1, hb = u & 1;
+            const bool is_x = slot < P, is_y = slot >= P8 && slot < P8 + Qw;
+            valid[i] = is_x || is_y;
+            const int c = is_x ? slot : (is_y ? P + (slot - P8) : 0);  // X columns, then Y columns
+            rq[i] = 8 * g + 4 * hb;
+            owner[i] = valid[i] && (u & 0x11) == 0;
+            col[i] = c;
             e[i] = E_NONE;
             if (c < P) {
                 src[i] = reinterpret_cast<const char*>(prm.X + c);
                 ldb[i] = prm.ldx * 8;
                 // slice s in operand-A block (stacked ? s / 2 : s), row (stacked ? (s % 2) * 64 : 0) + c
-                off0[i] = kmajor_off(c, g) + hb;
+                off0[i] = kmajor_off(c, g) + 8 * hb;
                 dsl[i] = stacked ? 2048u : 4096u;
             } else {
                 src[i] = reinterpret_cast<const char*>(prm.Y + q0 + (c - P));
                 ldb[i] = prm.ldy * 8;
-                off0[i] = L.a_bytes + kmajor_off(c - P, g) + hb;
+                off0[i] = L.a_bytes + kmajor_off(c - P, g) + 8 * hb;
                 dsl[i] = (uint32_t)Qp * 32u;
             }
         }
@@ -449,7 +468,7 @@ __global__ void __launch_bounds__(block_threads<PER>(), 1) k_split(const Params 
                 for (int r = 0; r < 4; ++r)
                     hm = max(hm, (uint32_t)((unsigned long long)__double_as_longlong(v[i][r]) >> 32) & 0x7FFFFFFFu);
                 hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, 1));
-                hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, 2));
+                hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, 16));
                 const int em = exp_from_hi(hm);
                 if (valid[i] && em > e[i]) {
                     e[i] = em;
@@ -471,7 +490,7 @@ __global__ void __launch_bounds__(block_threads<PER>(), 1) k_split(const Params 
 #pragma unroll
             for (int i = 0; i < PER; ++i) {
                 if (!valid[i]) continue;
-                if (owner[i]) ex[(ct + i * NCONV) >> 2] = e[i];
+                if (owner[i]) ex[col[i]] = e[i];
                 uint32_t w[NSLICE][2];
 #pragma unroll
                 for (int r = 0; r < 4; r += 2) {
