@@ -56,6 +56,8 @@
 
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "tsm_internal.h"
 #include "tsm_split.h"
 
@@ -313,6 +315,25 @@ __device__ __forceinline__ void split_pair(double xa, double xb, int e, uint32_t
     w[3] = fin(m23, 0x4140, c_low);  // byte 2
     w[4] = fin(m01, 0x4342, c_low);  // byte 1
     w[5] = fin(m01, 0x4140, c_low);  // byte 0
+}
+
+// W = sum_d P_d 2^(8(5-d)) for accumulator entry qq of the six blocks v[j]
+// (tensor-memory words, FP32 integers): block j holds weight d = j + H (rows of
+// the second stacked slice: H = 1; their d = 6 block is dropped).  Split as
+// 2^32 (P_0 2^8 + P_1) + P_2 2^24 + P_3 2^16 + P_4 2^8 + P_5: |P_0| <= 2^22
+// and |P_1| <= 2^23 keep the first part in 31 bits, the rest are exact 64-bit
+// multiply-adds.
+template <int H>
+__device__ __forceinline__ long long combine_w(const uint32_t (&v)[NSLICE][8], int qq) {
+    int pd[NSLICE];
+#pragma unroll
+    for (int d = 0; d < NSLICE; ++d) pd[d] = d >= H ? __float2int_rn(__uint_as_float(v[d - H][qq])) : 0;
+    long long lo = (long long)pd[5];
+    lo += (long long)pd[4] * 256;
+    lo += (long long)pd[3] * 65536;
+    lo += (long long)pd[2] * 16777216;
+    const int hi = pd[0] * 256 + pd[1];
+    return (long long)((unsigned long long)lo + ((unsigned long long)(unsigned int)hi << 32));
 }
 
 // Exponent from the largest magnitude high word of a column: |x| < 2^e for
@@ -697,34 +718,36 @@ __global__ void __launch_bounds__(block_threads<PER>(), 1) k_split(const Params 
             }
             const int* ex = snap + slot * NE;
             const int ep = prow ? ex[p] : 0;
-            for (int qb = qlo; qb < qhi; qb += 8) {
-                uint32_t v[NSLICE][8];
+            // the weight offset of a warp's rows is warp-uniform: one loop per value
+            auto drain = [&](auto half_tag) {
+                constexpr int H = decltype(half_tag)::value;
+                for (int qb = qlo; qb < qhi; qb += 8) {
+                    uint32_t v[NSLICE][8];
 #pragma unroll
-                for (int j = 0; j < NSLICE; ++j)
-                    tmem_ld8(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(j * Qp + qb), v[j]);
-                tmem_wait_ld();
+                    for (int j = 0; j < NSLICE; ++j)
+                        tmem_ld8(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(j * Qp + qb), v[j]);
+                    tmem_wait_ld();
 #pragma unroll
-                for (int qq = 0; qq < 8; ++qq) {
-                    const int q = qb + qq;
-                    if (!prow || q >= Qw) continue;
-                    long long W = 0;
-#pragma unroll
-                    for (int j = 0; j < NSLICE; ++j) {
-                        const int dd = j + half;
-                        if (dd < NSLICE)
-                            W += (long long)__float2int_rn(__uint_as_float(v[j][qq])) << (8 * (NSLICE - 1 - dd));
+                    for (int qq = 0; qq < 8; ++qq) {
+                        const int q = qb + qq;
+                        if (!prow || q >= Qw) continue;
+                        const long long W = combine_w<H>(v, qq);
+                        if (W == 0) continue;
+                        long long* ap = &iacc[q * 128 + row];
+                        const long long a = *ap;
+                        long long sum = (long long)((unsigned long long)a + (unsigned long long)W);
+                        if (((a ^ sum) & (W ^ sum)) < 0) {  // would overflow: move a to binary64
+                            flush[q * 128 + row] += scaled(a, ep + ex[P + q] - 54);
+                            sum = W;
+                        }
+                        *ap = sum;
                     }
-                    if (W == 0) continue;
-                    long long* ap = &iacc[q * 128 + row];
-                    const long long a = *ap;
-                    long long sum = (long long)((unsigned long long)a + (unsigned long long)W);
-                    if (((a ^ sum) & (W ^ sum)) < 0) {  // would overflow: move a to binary64
-                        flush[q * 128 + row] += scaled(a, ep + ex[P + q] - 54);
-                        sum = W;
-                    }
-                    *ap = sum;
                 }
-            }
+            };
+            if (half)
+                drain(std::integral_constant<int, 1>());
+            else
+                drain(std::integral_constant<int, 0>());
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(bar(M_TMEM_EMPTY));
