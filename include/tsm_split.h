@@ -45,6 +45,30 @@ tsm_status tsm_tsmttsm_split(tsm_op opA, tsm_dtype dtype, int M, int N,
                              tsm_stream_t stream);
 
 /*
+ * Launch plan of tsm_tsmttsm_split for a shape (no work is done).  Narrow
+ * products (accumulators of 6 slices x the Y chunk width in few tensor-memory
+ * columns) run several CTAs per SM so that one CTA's tensor-memory drain
+ * overlaps another's conversion; wide ones run one CTA per SM and split B's
+ * columns into two chunks when they exceed tensor memory.
+ * Errors: info == NULL, bad dtype or K < 1 -> INVALID_VALUE; M, N outside
+ * [1, 64] -> NOT_SUPPORTED; no sm_103 device -> NO_DEVICE.
+ */
+typedef struct {
+    int ctas;              /* CTAs of the split kernel */
+    int ctas_per_sm;       /* co-resident CTAs per SM (1..4) */
+    int column_chunks;     /* B column chunks (1 or 2) */
+    int converter_threads; /* threads per CTA that split the inputs */
+    int epilogue_warps;    /* warps per CTA that drain tensor memory */
+    int threads_per_cta;
+    int digit_stages;      /* depth of the converter -> tensor-core ring */
+    int tmem_columns;      /* tensor-memory columns allocated per CTA */
+    int smem_bytes;        /* dynamic shared memory per CTA */
+} tsm_split_plan_info;
+
+tsm_status tsm_split_plan(tsm_dtype dtype, int M, int N, int64_t K,
+                          tsm_split_plan_info *info);
+
+/*
  * Synchronizes `stream` and reports whether the most recent
  * tsm_tsmttsm_split on it hit a bounded device-side wait that gave up
  * (TSM_ERR_TIMEOUT; that call's C then holds NaN) -- TSM_OK otherwise.

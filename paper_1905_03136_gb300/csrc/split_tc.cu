@@ -23,8 +23,9 @@
 // grows, when it would overflow, and at the end.  Partials of all CTAs are
 // reduced in a fixed order.
 //
-// CTA organisation (one CTA per SM, persistent over a contiguous K range and
-// a chunk of Y's columns):
+// CTA organisation (one to four CTAs per SM, as tensor memory and shared
+// memory allow; each persistent over a contiguous K range and a chunk of Y's
+// columns):
 //   converter warps  each thread owns one or two fixed "units" (4 rows of
 //                    one column in every 16-row step) and keeps the global
 //                    loads of its next one or two steps in flight in
@@ -39,9 +40,10 @@
 //                    decides the tile boundaries (a stamped stage, or 16
 //                    steps); the warp copies the tile's exponents for the
 //                    epilogue;
-//   8 epilogue warps two per tensor-memory lane quarter, each on half of
-//                    the columns: drain tensor memory after each tile
-//                    (tcgen05.ld) and accumulate.
+//   epilogue warps   8 (two per tensor-memory lane quarter, each on half
+//                    of the columns) or, with several CTAs per SM, 4:
+//                    drain tensor memory after each tile (tcgen05.ld) and
+//                    accumulate.
 // MMA operand A (M = 128 rows): X slices, two slices per 128-row block when
 // P <= 64 ("stacked"), one slice per block when 64 < P <= 128.  Operand B
 // (N rows): the six Y slices stacked, Qp rows each.  Accumulator column
@@ -70,8 +72,8 @@ constexpr int NSLICE = 6;           // 8-bit slices per input
 constexpr int NDIG_MAX = 6;         // digit stages (converters -> MMA): as many as fit, up to this
 constexpr int NEXP = 4;             // exponent snapshot ring (MMA warp -> epilogue)
 constexpr int MAX_MMAS = 9;         // MMAs per step (six slices of X against the Y slices, N <= 256 each)
-constexpr int NEPI_WARPS = 8;
-constexpr int TMEM_COLS = 512;
+constexpr int NEPI_MAX = 8;         // epilogue warps: 8 (two per lane quarter) or 4
+constexpr int TMEM_COLS_MAX = 512;
 constexpr int E_NONE = -4000;       // running exponent before any nonzero value
 constexpr long long kDefaultTimeout = 4000000000ll;  // SM cycles (~2 s)
 
@@ -89,7 +91,7 @@ struct Conv<2> {
 };
 template <int PER>
 constexpr int block_threads() {
-    return Conv<PER>::MAX_THREADS + (1 + NEPI_WARPS) * 32;
+    return Conv<PER>::MAX_THREADS + (1 + NEPI_MAX) * 32;
 }
 
 struct Params {
@@ -105,6 +107,10 @@ struct Params {
     int stacked;  // P <= 64
     int Qp;       // padded chunk width (multiple of 16)
     int nconv;    // converter threads (multiple of 32); the MMA warp and the epilogue warps follow
+    int nepi;     // epilogue warps: 4 (each on all columns) or 8 (two per lane quarter, half the columns each)
+    int tmem_cols;  // tensor-memory columns allocated: a power of two >= 6 * Qp
+    int smem_budget;  // bytes of shared memory the layout may use (several CTAs per SM share 228 KB)
+    int smem_floor;   // minimum dynamic shared memory: keeps more CTAs than planned off an SM
     double* ws;     // [n_kr][P][Q]
     double* flush;  // [CTA][Qp][128]: binary64 totals of the epilogue lanes
     int* err;
@@ -219,10 +225,12 @@ struct Layout {
     uint32_t total;
 };
 
-constexpr uint32_t kSmemBudget = 227u * 1024u;
+constexpr uint32_t kSmemBudget = 227u * 1024u;  // one CTA per SM
+constexpr uint32_t kSmemPerSM = 228u * 1024u;   // shared by the CTAs of an SM, 1 KB reserved per CTA
 constexpr uint32_t kMiscBytes = 256u;
 
-__host__ __device__ inline Layout make_layout(int P, int Qp, int Qw, int stacked) {
+__host__ __device__ inline Layout make_layout(int P, int Qp, int Qw, int stacked, uint32_t budget,
+                                              uint32_t floor_bytes) {
     Layout L;
     L.nrb = stacked ? 3 : 6;
     L.units = 32 * ((((P + 7) & ~7) + Qw + 7) / 8);  // 4 units per column slot, 8 slots per group of 32
@@ -233,7 +241,7 @@ __host__ __device__ inline Layout make_layout(int P, int Qp, int Qw, int stacked
     const uint32_t acc = (uint32_t)Qp * 128u * 8u;
     const uint32_t exps = (uint32_t)L.ne * 4u;
     const uint32_t fixed = acc + NEXP * exps + kMiscBytes + 256u;  // + alignment slack
-    int ndig = kSmemBudget > fixed ? (int)((kSmemBudget - fixed) / (L.stage + exps)) : 0;
+    int ndig = budget > fixed ? (int)((budget - fixed) / (L.stage + exps)) : 0;
     if (ndig > NDIG_MAX) ndig = NDIG_MAX;
     L.ndig = ndig;  // the host rejects fewer than 2
     L.dig_off = 0;
@@ -242,7 +250,7 @@ __host__ __device__ inline Layout make_layout(int P, int Qp, int Qw, int stacked
     L.snap_off = L.exps_off + (uint32_t)ndig * exps;
     L.misc_off = (L.snap_off + NEXP * exps + 127u) & ~127u;
     L.total = L.misc_off + kMiscBytes;
-    if (L.total < 120u * 1024u) L.total = 120u * 1024u;  // one CTA per SM (tensor memory is taken whole)
+    if (L.total < floor_bytes) L.total = floor_bytes;  // no more CTAs per SM than tensor memory was split for
     return L;
 }
 
@@ -364,7 +372,7 @@ __global__ void __launch_bounds__(block_threads<PER>(), 1) k_split(const Params 
     const int Qp = prm.Qp;
     const int64_t Ktot = prm.K;
     const int stacked = prm.stacked;
-    const Layout L = make_layout(P, Qp, Qw, stacked);
+    const Layout L = make_layout(P, Qp, Qw, stacked, (uint32_t)prm.smem_budget, (uint32_t)prm.smem_floor);
     const int NE = L.ne, ndig = L.ndig;
     unsigned char* dig = smem + L.dig_off;
     long long* iacc = reinterpret_cast<long long*>(smem + L.acc_off);
@@ -399,9 +407,9 @@ __global__ void __launch_bounds__(block_threads<PER>(), 1) k_split(const Params 
             mbar_init(bar(M_DIG_EMPTY + 8 * i), 1);
             chg_step[i] = -1;
         }
-        for (int i = 0; i < NEXP; ++i) mbar_init(bar(M_EXP_EMPTY + 8 * i), NEPI_WARPS);
+        for (int i = 0; i < NEXP; ++i) mbar_init(bar(M_EXP_EMPTY + 8 * i), prm.nepi);
         mbar_init(bar(M_TILE_FULL), 1);
-        mbar_init(bar(M_TMEM_EMPTY), NEPI_WARPS);
+        mbar_init(bar(M_TMEM_EMPTY), prm.nepi);
         mbar_init(bar(M_MMA_DONE), 1);
         *abort_flag = 0;
         fence_mbar_init();
@@ -410,7 +418,7 @@ __global__ void __launch_bounds__(block_threads<PER>(), 1) k_split(const Params 
     if (warp == MMA_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          bar(M_TMEM_SLOT)),
-                     "r"(TMEM_COLS));
+                     "r"(prm.tmem_cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
@@ -675,15 +683,15 @@ __global__ void __launch_bounds__(block_threads<PER>(), 1) k_split(const Params 
         // shared memory, at the scale of the current column exponents.  It
         // moves to binary64 (`flush`, this thread's own entries in global
         // memory) only when an exponent grows, when the integer sum would
-        // overflow, and at the end -- not once per tile.  Warps w and w + 4
-        // share a lane quarter and split the columns.
+        // overflow, and at the end -- not once per tile.  With 8 warps,
+        // warps w and w + 4 share a lane quarter and split the columns.
         const int ew = warp - EPI_WARP0;
         const int lane_base = 32 * (warp & 3);
         const int row = lane_base + lane;  // TMEM lane = accumulator row
         const int p = stacked ? (row & 63) : row;
         const int half = stacked ? (row >> 6) : 0;
         const bool prow = p < P;
-        const int qh = Qp / 2;  // a multiple of 8
+        const int qh = prm.nepi == 8 ? Qp / 2 : Qp;  // a multiple of 8
         const int qlo = (ew >> 2) * qh, qhi = qlo + qh;
         double* flush = prm.flush + (int64_t)blockIdx.x * Qp * 128;
         for (int q = qlo; q < qhi; ++q) flush[q * 128 + row] = 0.0;
@@ -775,7 +783,7 @@ __global__ void __launch_bounds__(block_threads<PER>(), 1) k_split(const Params 
     __syncthreads();
     if (warp == MMA_WARP) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(prm.tmem_cols));
     }
 }
 
@@ -838,6 +846,120 @@ tsm_status validate_common(int dtype, int M, int N, int64_t K, const double* alp
 
 using namespace tsm;
 
+namespace tsm {
+namespace split {
+
+// Everything about a launch that depends on the shape only.
+struct Plan {
+    Params prm;     // shape fields filled; pointers, workspace and timeout are the caller's
+    Layout L;
+    int per = 1;    // converter units per thread
+    int cps = 0;    // CTAs per SM
+    int threads = 0;
+    const void* fn = nullptr;
+};
+
+tsm_status make_plan(int cplx, int M, int N, int64_t K, Plan* pl) {
+    const DeviceInfo& di = device_info();
+    Params& prm = pl->prm;
+    const int c = cplx ? 2 : 1;
+    const int P = M * c, Q = N * c;
+    prm.P = P;
+    prm.Q = Q;
+    prm.K = K;
+    prm.stacked = P <= 64 ? 1 : 0;
+    // Y column chunks: one if 6 slices of it fit tensor memory, else two
+    // chunks split on an even column
+    if (Q <= 80) {
+        prm.n_qc = 1;
+        prm.q0[0] = 0;
+        prm.qw[0] = Q;
+        prm.q0[1] = 0;
+        prm.qw[1] = 0;
+    } else {
+        int q1 = ((Q / 2) + 1) & ~1;
+        prm.n_qc = 2;
+        prm.q0[0] = 0;
+        prm.qw[0] = q1;
+        prm.q0[1] = q1;
+        prm.qw[1] = Q - q1;
+    }
+    const int qmax = prm.qw[0] > prm.qw[1] ? prm.qw[0] : prm.qw[1];
+    prm.Qp = (qmax + 15) & ~15;
+    if (count_mmas(prm.stacked, prm.Qp) > MAX_MMAS) return TSM_ERR_NOT_SUPPORTED;
+
+    // CTA shape.  Accumulators take 6 * Qp tensor-memory columns; the
+    // allocation is the next power of two, so narrow chunks leave room for
+    // several CTAs per SM, which then overlap one another's waits (drains,
+    // load latency).  Shared memory is split between them and padded so that
+    // no more CTAs than planned share an SM (a further one would block in its
+    // tensor-memory allocation).
+    int tcols = 32;
+    while (tcols < 6 * prm.Qp) tcols <<= 1;
+    prm.tmem_cols = tcols;
+    const int units = 32 * ((((P + 7) & ~7) + qmax + 7) / 8);  // as make_layout
+    pl->per = units <= Conv<1>::MAX_THREADS ? 1 : 2;
+    prm.nconv = (((units + pl->per - 1) / pl->per) + 31) & ~31;
+    if (prm.nconv > (pl->per == 1 ? Conv<1>::MAX_THREADS : Conv<2>::MAX_THREADS)) return TSM_ERR_NOT_SUPPORTED;
+    pl->fn = pl->per == 1 ? (const void*)k_split<1> : (const void*)k_split<2>;
+    if (cudaFuncSetAttribute(pl->fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
+        return TSM_ERR_LAUNCH;
+    int cps_max = TMEM_COLS_MAX / tcols;
+    if (cps_max > 4) cps_max = 4;
+    // Co-residency is counted here from the kernel's registers and the SM's
+    // limits (the occupancy query reports one CTA for this kernel although
+    // two measurably run together): registers per warp are allocated in
+    // units of 256 from each of the 4 sub-partitions' 16K, and every CTA's
+    // shared memory carries a 1 KB reserve.
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, pl->fn) != cudaSuccess) return TSM_ERR_LAUNCH;
+    const int regs_per_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+    const int warps_per_sm = regs_per_warp > 0 ? 4 * (16384 / regs_per_warp) : 64;
+    auto fits = [&](int thr, uint32_t smem) {
+        const int by_regs = warps_per_sm / (thr / 32);
+        const int by_smem = (int)(kSmemPerSM / (smem + 1024u));
+        const int by_thr = 2048 / thr;
+        return min(min(by_regs, by_smem), min(by_thr, 32));
+    };
+    pl->cps = 0;
+    for (int cc = cps_max; cc >= 1 && !pl->cps; --cc) {
+        // several CTAs per SM share the drains: 4 epilogue warps each; alone, 8
+        const int nepi = cc > 1 ? 4 : 8;
+        const int thr = prm.nconv + (1 + nepi) * 32;
+        const uint32_t budget = cc == 1 ? kSmemBudget : ((kSmemPerSM / cc - 1024u) & ~127u);
+        const uint32_t floor_b = kSmemPerSM / (cc + 1);
+        const Layout L = make_layout(P, prm.Qp, qmax, prm.stacked, budget, floor_b);
+        if (L.ndig < (cc > 1 ? 3 : 2) || L.total > (uint32_t)di.smem_optin) continue;
+        if (fits(thr, L.total) == cc) {
+            pl->cps = cc;
+            pl->threads = thr;
+            pl->L = L;
+            prm.nepi = nepi;
+            prm.smem_budget = (int)budget;
+            prm.smem_floor = (int)floor_b;
+        }
+    }
+    if (!pl->cps) return TSM_ERR_NOT_SUPPORTED;
+    // the dynamic shared memory size of the chosen layout (the loop may have
+    // set a larger one while trying more CTAs per SM)
+    if (cudaFuncSetAttribute(pl->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->L.total) != cudaSuccess)
+        return TSM_ERR_LAUNCH;
+
+    const int64_t steps = (K + KSTEP - 1) / KSTEP;
+    int n_kr = pl->cps * di.sm_count / prm.n_qc;
+    if (n_kr < 1) n_kr = 1;
+    if ((int64_t)n_kr > steps) n_kr = (int)(steps > 0 ? steps : 1);
+    prm.steps_per_kr = (steps + n_kr - 1) / n_kr;
+    if (prm.steps_per_kr < 1) prm.steps_per_kr = 1;
+    n_kr = (int)((steps + prm.steps_per_kr - 1) / prm.steps_per_kr);
+    if (n_kr < 1) n_kr = 1;
+    prm.n_kr = n_kr;
+    return TSM_OK;
+}
+
+}  // namespace split
+}  // namespace tsm
+
 extern "C" tsm_status tsm_tsmttsm_split(tsm_op opA, tsm_dtype dtype, int M, int N, int64_t K,
                                         const double* alpha, const void* A, int64_t lda, const void* B,
                                         int64_t ldb, const double* beta, void* C, int64_t ldc,
@@ -861,44 +983,16 @@ extern "C" tsm_status tsm_tsmttsm_split(tsm_op opA, tsm_dtype dtype, int M, int 
                    ? TSM_OK
                    : TSM_ERR_LAUNCH;
     }
+    split::Plan pl;
+    if ((st = split::make_plan(cplx, M, N, K, &pl)) != TSM_OK) return st;
+    split::Params& prm = pl.prm;
     const int c = cplx ? 2 : 1;
-    const int P = M * c, Q = N * c;
-    const int64_t ldx = lda * c, ldy = ldb * c;
-    split::Params prm;
     prm.X = (const double*)A;
-    prm.ldx = ldx;
+    prm.ldx = lda * c;
     prm.Y = (const double*)B;
-    prm.ldy = ldy;
-    prm.P = P;
-    prm.Q = Q;
-    prm.K = K;
-    prm.stacked = P <= 64 ? 1 : 0;
-    // Y column chunks: one if 6 slices of it fit tensor memory, else two
-    // chunks split on an even column
-    if (Q <= 80) {
-        prm.n_qc = 1;
-        prm.q0[0] = 0;
-        prm.qw[0] = Q;
-        prm.q0[1] = 0;
-        prm.qw[1] = 0;
-    } else {
-        int q1 = ((Q / 2) + 1) & ~1;
-        prm.n_qc = 2;
-        prm.q0[0] = 0;
-        prm.qw[0] = q1;
-        prm.q0[1] = q1;
-        prm.qw[1] = Q - q1;
-    }
-    int qmax = prm.qw[0] > prm.qw[1] ? prm.qw[0] : prm.qw[1];
-    prm.Qp = (qmax + 15) & ~15;
-    const int64_t steps = (K + split::KSTEP - 1) / split::KSTEP;
-    int n_kr = di.sm_count / prm.n_qc;
-    if (n_kr < 1) n_kr = 1;
-    if ((int64_t)n_kr > steps) n_kr = (int)steps;
-    prm.steps_per_kr = (steps + n_kr - 1) / n_kr;
-    n_kr = (int)((steps + prm.steps_per_kr - 1) / prm.steps_per_kr);
-    prm.n_kr = n_kr;
+    prm.ldy = ldb * c;
     prm.timeout = split::g_timeout;
+    const int n_kr = prm.n_kr, P = prm.P, Q = prm.Q;
 
     Workspace* ws = nullptr;
     const size_t part = (size_t)n_kr * P * Q * sizeof(double);
@@ -907,30 +1001,39 @@ extern "C" tsm_status tsm_tsmttsm_split(tsm_op opA, tsm_dtype dtype, int M, int 
     prm.ws = ws->partials;
     prm.flush = ws->partials + (size_t)n_kr * P * Q;
     prm.err = reinterpret_cast<int*>(ws->tickets) + 32;  // error word of this stream
-    const split::Layout L = split::make_layout(P, prm.Qp, qmax, prm.stacked);
-    if (L.ndig < 2 || L.total > di.smem_optin || split::count_mmas(prm.stacked, prm.Qp) > split::MAX_MMAS)
-        return TSM_ERR_NOT_SUPPORTED;
-    // converters: one unit per thread when the units fit one thread each
-    // (two steps of loads in flight), else two (one step in flight)
-    const int per = L.units <= split::Conv<1>::MAX_THREADS ? 1 : 2;
-    prm.nconv = (((L.units + per - 1) / per) + 31) & ~31;
-    if (prm.nconv > (per == 1 ? split::Conv<1>::MAX_THREADS : split::Conv<2>::MAX_THREADS))
-        return TSM_ERR_NOT_SUPPORTED;
-    const void* fn = per == 1 ? (const void*)split::k_split<1> : (const void*)split::k_split<2>;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) != cudaSuccess)
-        return TSM_ERR_LAUNCH;
     if (cudaMemsetAsync(prm.err, 0, sizeof(int), s) != cudaSuccess) return TSM_ERR_LAUNCH;
-    const int threads = prm.nconv + (1 + split::NEPI_WARPS) * 32;
-    if (per == 1)
-        split::k_split<1><<<n_kr * prm.n_qc, threads, L.total, s>>>(prm);
+    if (pl.per == 1)
+        split::k_split<1><<<n_kr * prm.n_qc, pl.threads, pl.L.total, s>>>(prm);
     else
-        split::k_split<2><<<n_kr * prm.n_qc, threads, L.total, s>>>(prm);
+        split::k_split<2><<<n_kr * prm.n_qc, pl.threads, pl.L.total, s>>>(prm);
     if (cudaGetLastError() != cudaSuccess) return TSM_ERR_LAUNCH;
     const int outs = M * N;
     split::k_split_combine<<<(outs + 127) / 128, 128, 0, s>>>(
         ws->partials, n_kr, P, Q, M, N, cplx, (cplx && opA == TSM_OP_C) ? 1 : 0, alpha[0], cplx ? alpha[1] : 0.0,
         beta[0], cplx ? beta[1] : 0.0, beta_zero, (double*)C, ldc, prm.err);
     if (cudaGetLastError() != cudaSuccess) return TSM_ERR_LAUNCH;
+    return TSM_OK;
+}
+
+extern "C" tsm_status tsm_split_plan(tsm_dtype dtype, int M, int N, int64_t K, tsm_split_plan_info* info) {
+    if (!info || (dtype != TSM_R64 && dtype != TSM_C64) || K < 1) return TSM_ERR_INVALID_VALUE;
+    if (M < 1 || N < 1 || M > 64 || N > 64) return TSM_ERR_NOT_SUPPORTED;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TSM_ERR_NO_DEVICE;
+    const DeviceInfo& di = device_info();
+    if (di.cc_major != 10 || di.cc_minor != 3) return TSM_ERR_NO_DEVICE;
+    split::Plan pl;
+    const tsm_status st = split::make_plan(dtype == TSM_C64, M, N, K, &pl);
+    if (st != TSM_OK) return st;
+    info->ctas = pl.prm.n_kr * pl.prm.n_qc;
+    info->ctas_per_sm = pl.cps;
+    info->column_chunks = pl.prm.n_qc;
+    info->converter_threads = pl.prm.nconv;
+    info->epilogue_warps = pl.prm.nepi;
+    info->threads_per_cta = pl.threads;
+    info->digit_stages = pl.L.ndig;
+    info->tmem_columns = pl.prm.tmem_cols;
+    info->smem_bytes = (int)pl.L.total;
     return TSM_OK;
 }
 

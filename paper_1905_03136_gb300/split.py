@@ -5,7 +5,15 @@ import ctypes
 from . import _lib
 from ._lib import scalar
 
+class PlanInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in ("ctas", "ctas_per_sm", "column_chunks", "converter_threads",
+                                              "epilogue_warps", "threads_per_cta", "digit_stages", "tmem_columns",
+                                              "smem_bytes")]
+
+
 _lib.extend_signatures({
+    "tsm_split_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                      ctypes.POINTER(PlanInfo)]),
     "tsm_tsmttsm_split": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_int64,
                                          ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
@@ -42,3 +50,11 @@ def status(stream=None):
 
 def set_timeout(cycles):
     _lib.call("tsm_split_set_timeout", int(cycles))
+
+
+def plan(dtype, M, N, K):
+    """The launch plan (dict) tsm_tsmttsm_split would use for a shape;
+    dtype is 0 (real) or 1 (complex)."""
+    info = PlanInfo()
+    _lib.call("tsm_split_plan", int(dtype), int(M), int(N), int(K), ctypes.byref(info))
+    return {n: getattr(info, n) for n, _ in PlanInfo._fields_}

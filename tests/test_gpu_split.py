@@ -142,7 +142,26 @@ def test_split_wait_expiry_reports_timeout(sp):
 K_FULL = 1 << 24
 
 
-@pytest.mark.parametrize("case", [(True, 64, 64), (True, 32, 32), (True, 48, 48), (False, 64, 64)],
+def test_split_plan(sp):
+    """Narrow products share SMs (several CTAs, smaller tensor-memory
+    allocations); wide ones take one CTA per SM and two column chunks."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for (dt, M, N) in [(0, 1, 1), (0, 16, 16), (1, 8, 8), (0, 32, 32), (1, 16, 16), (0, 64, 64), (1, 32, 32),
+                       (1, 48, 48), (1, 64, 64), (1, 33, 41)]:
+        p = sp.plan(dt, M, N, K_FULL)
+        assert 1 <= p["ctas_per_sm"] <= 4
+        assert p["ctas"] == p["ctas_per_sm"] * sms // p["column_chunks"] * p["column_chunks"]
+        assert p["tmem_columns"] * p["ctas_per_sm"] <= 512
+        assert p["ctas_per_sm"] * (p["smem_bytes"] + 1024) <= 228 * 1024
+        assert p["digit_stages"] >= 2 and p["epilogue_warps"] in (4, 8)
+        assert p["threads_per_cta"] == p["converter_threads"] + 32 * (1 + p["epilogue_warps"])
+    assert sp.plan(0, 16, 16, K_FULL)["ctas_per_sm"] >= 2
+    wide = sp.plan(1, 64, 64, K_FULL)
+    assert wide["ctas_per_sm"] == 1 and wide["column_chunks"] == 2
+
+
+@pytest.mark.parametrize("case", [(True, 64, 64), (True, 32, 32), (True, 48, 48), (False, 64, 64), (False, 16, 16)],
                          ids=lambda c: "%s_%dx%d" % ("c64" if c[0] else "r64", c[1], c[2]))
 @pytest.mark.parametrize("dist", ["uniform", "loguniform"])
 def test_split_full_size_sampled(sp, case, dist):
