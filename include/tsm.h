@@ -130,6 +130,9 @@ typedef struct {
     int unroll;     /* rows per thread per loop iteration */
     int block;      /* threads per CTA */
     int generated;  /* 1 if emitted by the code generator */
+    int runtime_tile; /* 1: tile_m x tile_n (TSMTTSM) or threads_per_row x
+                         tile_n (TSMM) are maxima; each launch picks the size
+                         that pads M, N least (tsm_variant_shape) */
 } tsm_variant_info;
 
 /* Number of compiled variants of a product, or -1 for an unknown kind. */
@@ -138,6 +141,13 @@ int tsm_variant_count(tsm_kind kind);
 /* Describes variant `index` of `kind`.  INVALID_VALUE if out of range or
  * info is NULL. */
 tsm_status tsm_variant_get(tsm_kind kind, int index, tsm_variant_info *info);
+
+/* As tsm_variant_get, with the tile fields resolved for shape (M, N): for
+ * runtime-tile variants the tile (TSMTTSM) or threads per row and results
+ * per thread (TSMM) a launch of that shape uses.  INVALID_VALUE for a bad
+ * index or NULL info; NOT_SUPPORTED if the variant cannot run the shape. */
+tsm_status tsm_variant_shape(tsm_kind kind, int index, tsm_dtype dtype, int M, int N,
+                             tsm_variant_info *info);
 
 /* 1 if variant `index` can run (op, dtype, M, N), else 0. */
 int tsm_variant_supports(tsm_kind kind, int index, tsm_dtype dtype, int M, int N);

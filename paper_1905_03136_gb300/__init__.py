@@ -15,7 +15,7 @@ from . import _lib
 from ._lib import (C64, KIND_TSMM, KIND_TSMTTSM, OP_C, OP_N, OP_T, R64, TsmError, VariantInfo,
                    TuneSample, call, load, raw, scalar)
 
-__all__ = ["tsmttsm", "tsmm", "gs_step", "fill_random", "variants", "choose", "tune", "time_variant",
+__all__ = ["tsmttsm", "tsmm", "gs_step", "fill_random", "variants", "variant_shape", "choose", "tune", "time_variant",
            "TsmError", "load", "R64", "C64", "OP_T", "OP_C", "OP_N"]
 
 _OPS = {"T": OP_T, "C": OP_C, "N": OP_N, OP_T: OP_T, OP_C: OP_C, OP_N: OP_N}
@@ -131,6 +131,18 @@ def variants(kind):
         d["index"] = i
         out.append(d)
     return out
+
+
+def variant_shape(kind, index, dtype, M, N):
+    """Variant `index` described for shape (M, N): runtime-tile variants
+    report the tile (TSMTTSM) or threads per row and results per thread
+    (TSMM) their launch picks for it."""
+    info = VariantInfo()
+    call("tsm_variant_shape", kind, index, dtype, M, N, ctypes.byref(info))
+    d = {f: getattr(info, f) for f, _ in VariantInfo._fields_}
+    d["name"] = info.name.decode()
+    d["index"] = index
+    return d
 
 
 def choose(kind, dtype, M, N, K):

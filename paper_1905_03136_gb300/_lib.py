@@ -32,7 +32,7 @@ class VariantInfo(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 64), ("kind", ctypes.c_int), ("dtype", ctypes.c_int),
                 ("fixed_m", ctypes.c_int), ("fixed_n", ctypes.c_int), ("tile_m", ctypes.c_int),
                 ("tile_n", ctypes.c_int), ("threads_per_row", ctypes.c_int), ("unroll", ctypes.c_int),
-                ("block", ctypes.c_int), ("generated", ctypes.c_int)]
+                ("block", ctypes.c_int), ("generated", ctypes.c_int), ("runtime_tile", ctypes.c_int)]
 
 
 class TuneSample(ctypes.Structure):
@@ -52,6 +52,7 @@ SIGNATURES = {
     "tsm_tsmttsm_ex": (i32, [i32, i32, i32, i32, i64, dp, vp, i64, vp, i64, dp, vp, i64, i32, i32, vp]),
     "tsm_tsmm_ex": (i32, [i32, i32, i32, i32, i64, dp, vp, i64, vp, i64, dp, vp, i64, i32, i32, vp]),
     "tsm_gs_step": (i32, [i32, i32, i32, i64, vp, i64, vp, i64, vp, i64, vp]),
+    "tsm_variant_shape": (i32, [i32, i32, i32, i32, i32, ctypes.POINTER(VariantInfo)]),
     "tsm_status_string": (ctypes.c_char_p, [i32]),
     "tsm_version": (ctypes.c_char_p, []),
     "tsm_release": (i32, []),

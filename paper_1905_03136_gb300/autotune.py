@@ -62,7 +62,7 @@ def tune_shapes(kind, shapes, K, reps=3, log=None, flat=None):
         t0 = time.time()
         samples = tsm.tune(kind, X, Y, Z, reps=reps)
         for (v, g, ms) in samples:
-            vi = info[v]
+            vi = info[v] if not info[v].get("runtime_tile") else tsm.variant_shape(kind, v, int(cplx), M, N)
             rec = {"kind": kind, "dtype": int(cplx), "M": M, "N": N, "K": K, "variant": vi["name"],
                    "tile_m": vi["tile_m"], "tile_n": vi["tile_n"], "tpr": vi["threads_per_row"],
                    "unroll": vi["unroll"], "generated": vi["generated"], "fixed": int(vi["fixed_m"] > 0),

@@ -113,7 +113,9 @@ class CostModel:
 
 
 def candidates(kind, cplx, M, N):
-    """(variant index, grid, features-builder args) the exhaustive tuner would time."""
+    """(variant, grid) pairs the exhaustive tuner would time; each variant is
+    described for this shape (runtime-tile variants with the tile their
+    launch picks)."""
     import ctypes
     import paper_1905_03136_gb300 as tsm
     from . import _lib
@@ -122,6 +124,7 @@ def candidates(kind, cplx, M, N):
     for v in tsm.variants(kind):
         if not lib.tsm_variant_supports(kind, v["index"], int(cplx), M, N):
             continue
+        v = tsm.variant_shape(kind, v["index"], int(cplx), M, N)
         grids = (ctypes.c_int * 4)()
         n = ctypes.c_int()
         _lib.call("tsm_tune_grids", kind, v["index"], int(cplx), M, N, grids, 4, ctypes.byref(n))

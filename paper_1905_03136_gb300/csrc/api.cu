@@ -112,6 +112,7 @@ struct Registry {
     Registry() {
         register_fp64_variants(tsmttsm, tsmm);
         register_generated_variants(tsmttsm, tsmm);
+        register_rt_variants(tsmttsm, tsmm);
     }
 };
 
@@ -130,6 +131,7 @@ static bool variant_supports(const Variant& v, int dtype, int M, int N) {
     if (v.info.dtype != dtype) return false;
     if (v.info.fixed_m && v.info.fixed_m != M) return false;
     if (v.info.fixed_n && v.info.fixed_n != N) return false;
+    if (v.info.runtime_tile) return M >= 1 && N >= 1 && M <= 64 && N <= 64;  // a tile always exists
     if (v.info.kind == TSM_KIND_TSMTTSM) {
         const int P = ((M + v.info.tile_m - 1) / v.info.tile_m) * ((N + v.info.tile_n - 1) / v.info.tile_n);
         return P <= v.info.block;
@@ -162,7 +164,7 @@ static int heuristic_variant(tsm_kind kind, int dtype, int M, int N) {
             const int pm = (M + f.tile_m - 1) / f.tile_m, pn = (N + f.tile_n - 1) / f.tile_n;
             const double waste = (double)(pm * f.tile_m) * (pn * f.tile_n) / ((double)M * N);
             const int area = f.tile_m * f.tile_n;
-            if (area * (dtype == TSM_C64 ? 2 : 1) > 16) continue;
+            if (area * (dtype == TSM_C64 ? 2 : 1) > 32) continue;
             const bool better = waste < best_waste - 1e-9 ||
                                 (waste < best_waste + 1e-9 && (area > best_area ||
                                                                (area == best_area && f.unroll > best_u)));
@@ -181,6 +183,14 @@ static int heuristic_variant(tsm_kind kind, int dtype, int M, int N) {
         int nptv = npt <= 1 ? 1 : npt <= 2 ? 2 : npt <= 4 ? 4 : npt <= 8 ? 8 : 16;
         const int u = nptv >= 8 ? 1 : (nptv >= 4 ? (tpr == 16 ? 2 : 2) : (nptv == 2 ? (tpr >= 8 ? 2 : 4) : 4));
         snprintf(name, sizeof(name), "tsmm_%s_smemc_tpr%d_npt%d_u%d", dt, tpr, nptv, u);
+        // widths the power-of-two thread counts do not cover exactly: the
+        // runtime variant (any threads per row, so no padded result slots)
+        if (npt * tpr != N) {
+            char rt[64];
+            snprintf(rt, sizeof(rt), "tsmm_%s_rt_npt4_u2", dt);
+            const int r = find(rt);
+            if (r >= 0) return r;
+        }
         int idx = find(name);
         if (idx >= 0) return idx;
         for (size_t i = 0; i < t.size(); ++i)
@@ -428,6 +438,17 @@ tsm_status tsm_variant_get(tsm_kind kind, int index, tsm_variant_info* info) {
     const Variant* v = variant_at(kind, index);
     if (!v || !info) return TSM_ERR_INVALID_VALUE;
     *info = v->info;
+    return TSM_OK;
+}
+
+tsm_status tsm_variant_shape(tsm_kind kind, int index, tsm_dtype dtype, int M, int N, tsm_variant_info* info) {
+    const Variant* v = variant_at(kind, index);
+    if (!v || !info) return TSM_ERR_INVALID_VALUE;
+    if (!variant_supports(*v, dtype, M, N)) return TSM_ERR_NOT_SUPPORTED;
+    *info = v->info;
+    if (v->info.runtime_tile) {
+        if (kind == TSM_KIND_TSMM) rt_tsmm_tpr(N, v->info.tile_n, &info->threads_per_row, &info->tile_n);
+    }
     return TSM_OK;
 }
 

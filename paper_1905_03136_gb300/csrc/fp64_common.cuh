@@ -43,9 +43,11 @@ __device__ __forceinline__ void sum_partials(const double* ws, int MNc, int o, i
 //      launch.
 // Every order above depends only on (G, M, N, tile), so results repeat bit
 // for bit.
+// Kernels with a tile chosen at launch pass its size (tm <= TM, tn <= TN;
+// warp-uniform, so skipped entries cost nothing).
 template <int TM, int TN, int CC>
 __device__ __forceinline__ void tsmttsm_finish(const TsmttsmArgs& a, const double* acc, int PM, int PN,
-                                               int L, int lane, int p, bool active) {
+                                               int L, int lane, int p, bool active, int tm = TM, int tn = TN) {
     __shared__ double red[kBlock * CC];
     __shared__ unsigned s_last;
     const int M = a.M, N = a.N;
@@ -59,6 +61,7 @@ __device__ __forceinline__ void tsmttsm_finish(const TsmttsmArgs& a, const doubl
         for (int j = 0; j < TN; ++j)
 #pragma unroll
             for (int c = 0; c < CC; ++c) {
+                if (i >= tm || j >= tn) continue;
                 if (active) red[lane * P + p] = acc[(i * TN + j) * CC + c];
                 __syncthreads();
                 for (int n = L; n > 1;) {

@@ -59,6 +59,10 @@ struct Variant {
 // build): hand-written families first, then code-generator output.
 void register_fp64_variants(std::vector<Variant>& tsmttsm, std::vector<Variant>& tsmm);
 void register_generated_variants(std::vector<Variant>& tsmttsm, std::vector<Variant>& tsmm);
+void register_rt_variants(std::vector<Variant>& tsmttsm, std::vector<Variant>& tsmm);
+
+// Per-launch choice of the runtime-threads-per-row TSMM variants (kernels_rt.cu).
+void rt_tsmm_tpr(int N, int nptmax, int* tpr, int* npt);
 
 // Device properties of the current device, cached.
 struct DeviceInfo {

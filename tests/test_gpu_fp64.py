@@ -47,9 +47,9 @@ def _variants_for(tsm, kind, dt, M, N):
 
 
 TSMTTSM_SHAPES = [(1, 1), (2, 2), (2, 3), (4, 4), (7, 5), (8, 8), (16, 16), (33, 17), (32, 32), (64, 64),
-                  (1, 64), (64, 1), (8, 32), (32, 8), (13, 64)]
+                  (1, 64), (64, 1), (8, 32), (32, 8), (13, 64), (49, 25)]
 TSMM_SHAPES = [(1, 1), (2, 2), (3, 5), (4, 4), (8, 8), (16, 16), (31, 7), (32, 32), (64, 64), (4, 64),
-               (64, 4), (1, 64), (64, 1)]
+               (64, 4), (1, 64), (64, 1), (54, 17), (28, 39)]
 
 
 @pytest.mark.parametrize("cplx", [False, True], ids=["r64", "c64"])
