@@ -625,21 +625,32 @@ def batched_configs_from_model(insts, model):
     kernel's codes (tile codes for TSMTTSM, threads-per-row codes for TSMM)."""
     import numpy as np
     from paper_1905_03136_gb300 import costmodel as cm
-    tiles = {1: (1, 1, 4), 2: (2, 2, 2), 3: (4, 4, 1), 4: (4, 8, 1), 5: (8, 4, 1)}
+    import paper_1905_03136_gb300 as tsm
+    tiles = {1: (1, 1, 4), 2: (2, 2, 2), 3: (4, 4, 1), 4: (4, 8, 1), 5: (8, 4, 1), 6: (3, 3, 2), 7: (2, 5, 2),
+             8: (5, 2, 2), 9: (3, 5, 1), 10: (5, 3, 1), 11: (2, 7, 1), 12: (7, 2, 1)}
     tprs = {1: 4, 2: 8, 3: 16}
+    rt = {v["dtype"]: v["index"] for v in tsm.variants(tsm.KIND_TSMM) if v["name"].endswith("_rt_npt4_u2")}
     cfg = []
     for (kind, cplx, M, N, K) in insts:
         cands, feats = [], []
         if kind == 0:
             for code, (tm, tn, u) in tiles.items():
+                if cplx and code in (4, 5):
+                    tm, tn = 4, 4  # complex runs these codes with a 4x4 tile
                 if math.ceil(M / tm) * math.ceil(N / tn) > 256:
                     continue
                 cands.append(code)
                 feats.append(cm.featurize(0, int(cplx), M, N, K, tm, tn, 1, u, 0, 0, 152))
         else:
             for code, tpr in tprs.items():
+                if cplx and code == 1:
+                    tpr = 8
                 cands.append(code)
                 feats.append(cm.featurize(1, int(cplx), M, N, K, 1, math.ceil(N / tpr), tpr, 2, 0, 0, 152))
+            shape = tsm.variant_shape(tsm.KIND_TSMM, rt[int(cplx)], int(cplx), M, N)
+            cands.append(4)
+            feats.append(cm.featurize(1, int(cplx), M, N, K, 1, shape["tile_n"], shape["threads_per_row"], 2, 0, 0,
+                                      152))
         pred = model.predict_log2_ineff(feats)
         cfg.append(cands[int(np.argmin(pred))])
     return cfg

@@ -17,6 +17,7 @@ namespace batched {
 
 struct Inst {
     int kind, cplx, conj, M, N, code, beta_zero, n_items;
+    int tpr;           // TSMM code 4: threads per row (any value 1..64)
     int64_t K, lda, ldb, ldo;
     const double* A;
     const double* B;
@@ -281,6 +282,111 @@ __device__ void tsmm_item(const Inst& in, const Item& it, double* cs) {
     __syncthreads();  // cs is reused by the next item
 }
 
+// TSMM item with any number of threads per row (in.tpr) and up to NPT
+// results each: npt * tpr covers N with the least padding, and the loop over
+// result slots has a warp-uniform bound, so no FMA is spent on padding.
+template <int NPT, bool CPLX>
+__device__ void tsmm_item_rt(const Inst& in, const Item& it, double* cs) {
+    constexpr int CC = CPLX ? 2 : 1;
+    constexpr int U = 2;
+    const int M = in.M, N = in.N, tpr = in.tpr;
+    for (int o = threadIdx.x; o < M * N; o += kThreads) {
+        const int m = o / N, n = o - m * N;
+        const double* src = in.B + ((int64_t)m * in.ldb + n) * CC;
+        if (!CPLX) {
+            cs[o] = in.ar * src[0];
+        } else {
+            const double cr = src[0], ci = src[CC - 1];
+            cs[o * CC] = in.ar * cr - in.ai * ci;
+            cs[o * CC + CC - 1] = in.ar * ci + in.ai * cr;
+        }
+    }
+    __syncthreads();
+    const int rpc = kThreads / tpr;
+    const int r = threadIdx.x / tpr, q = threadIdx.x - r * tpr;
+    const bool live = r < rpc;
+    const int npt = (N + tpr - 1) / tpr;
+    const int64_t sa = in.lda * CC, sb = in.ldo * CC;
+    for (int64_t base = it.r0; base < it.r1; base += (int64_t)rpc * U) {
+        int64_t row[U];
+        bool rok[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            row[u] = base + r + (int64_t)u * rpc;
+            rok[u] = live && row[u] < it.r1;
+            if (!rok[u]) row[u] = it.r0;
+        }
+        double acc[U][NPT][CC];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int j = 0; j < NPT; ++j)
+#pragma unroll
+                for (int c = 0; c < CC; ++c) acc[u][j][c] = 0.0;
+        if (live) {
+            for (int m0 = 0; m0 < M; m0 += 4) {
+                double av[4][U][CC];
+#pragma unroll
+                for (int mm = 0; mm < 4; ++mm)
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+#pragma unroll
+                        for (int c = 0; c < CC; ++c)
+                            av[mm][u][c] = (rok[u] && m0 + mm < M) ? __ldg(in.A + row[u] * sa + (m0 + mm) * CC + c) : 0.0;
+#pragma unroll
+                for (int mm = 0; mm < 4; ++mm) {
+                    const int m = m0 + mm;
+                    if (m >= M) break;
+#pragma unroll
+                    for (int j = 0; j < NPT; ++j) {
+                        if (j >= npt) break;
+                        const int n = q + j * tpr;
+                        if (n < N) {
+                            const double cr = cs[(m * N + n) * CC], ci = cs[(m * N + n) * CC + CC - 1];
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                if (!CPLX) {
+                                    acc[u][j][0] = fma(av[mm][u][0], cr, acc[u][j][0]);
+                                } else {
+                                    acc[u][j][0] = fma(av[mm][u][0], cr, acc[u][j][0]);
+                                    acc[u][j][0] = fma(-av[mm][u][CC - 1], ci, acc[u][j][0]);
+                                    acc[u][j][CC - 1] = fma(av[mm][u][0], ci, acc[u][j][CC - 1]);
+                                    acc[u][j][CC - 1] = fma(av[mm][u][CC - 1], cr, acc[u][j][CC - 1]);
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!rok[u]) continue;
+            double* out = in.out + row[u] * sb;
+#pragma unroll
+            for (int j = 0; j < NPT; ++j) {
+                if (j >= npt) break;
+                const int n = q + j * tpr;
+                if (n >= N) continue;
+                double vr = acc[u][j][0], vi = acc[u][j][CC - 1];
+                if (!CPLX) {
+                    if (!in.beta_zero) vr = fma(in.br, out[n], vr);
+                    out[n] = vr;
+                } else {
+                    if (!in.beta_zero) {
+                        const double orr = out[n * 2], oi = out[n * 2 + 1];
+                        vr += in.br * orr - in.bi * oi;
+                        vi += in.br * oi + in.bi * orr;
+                    }
+                    out[n * 2] = vr;
+                    out[n * 2 + 1] = vi;
+                }
+            }
+        }
+    }
+    __syncthreads();  // cs is reused by the next item
+}
+
 // -------------------------------------------------------- persistent kernel
 
 // Accumulators stay at <= 32 doubles per thread in every instantiation
@@ -304,6 +410,13 @@ __device__ void run_tsmttsm(const Inst& in, const Item& it, double* parts, unsig
             }
             tsmttsm_item<4, 4, 1, CPLX, CONJ>(in, it, parts, tickets, red);
             break;
+        case 6: tsmttsm_item<3, 3, 2, CPLX, CONJ>(in, it, parts, tickets, red); break;
+        case 7: tsmttsm_item<2, 5, 2, CPLX, CONJ>(in, it, parts, tickets, red); break;
+        case 8: tsmttsm_item<5, 2, 2, CPLX, CONJ>(in, it, parts, tickets, red); break;
+        case 9: tsmttsm_item<3, 5, 1, CPLX, CONJ>(in, it, parts, tickets, red); break;
+        case 10: tsmttsm_item<5, 3, 1, CPLX, CONJ>(in, it, parts, tickets, red); break;
+        case 11: tsmttsm_item<2, 7, 1, CPLX, CONJ>(in, it, parts, tickets, red); break;
+        case 12: tsmttsm_item<7, 2, 1, CPLX, CONJ>(in, it, parts, tickets, red); break;
         default: tsmttsm_item<4, 4, 1, CPLX, CONJ>(in, it, parts, tickets, red); break;
     }
 }
@@ -319,6 +432,7 @@ __device__ void run_tsmm(const Inst& in, const Item& it, double* cs) {
             tsmm_item<8, 8, CPLX>(in, it, cs);
             break;
         case 3: tsmm_item<16, 4, CPLX>(in, it, cs); break;
+        case 4: tsmm_item_rt<4, CPLX>(in, it, cs); break;
         default: tsmm_item<8, 8, CPLX>(in, it, cs); break;
     }
 }
@@ -354,10 +468,13 @@ __global__ void __launch_bounds__(kThreads) k_batched(const Inst* __restrict__ i
 
 // TSMTTSM tiles by code and the default choice: least padding waste, then
 // the larger tile (capped at 32 accumulator doubles), thread count <= 256.
-const int kTile[6][2] = {{0, 0}, {1, 1}, {2, 2}, {4, 4}, {4, 8}, {8, 4}};
+// (Complex data runs codes 4 and 5 with a 4x4 tile.)
+constexpr int kTileCodes = 12;
+const int kTile[kTileCodes + 1][2] = {{0, 0}, {1, 1}, {2, 2}, {4, 4}, {4, 8}, {8, 4}, {3, 3},
+                                      {2, 5}, {5, 2}, {3, 5}, {5, 3}, {2, 7}, {7, 2}};
 
 bool tile_ok(int code, int M, int N) {
-    if (code < 1 || code > 5) return false;
+    if (code < 1 || code > kTileCodes) return false;
     const int P = ((M + kTile[code][0] - 1) / kTile[code][0]) * ((N + kTile[code][1] - 1) / kTile[code][1]);
     return P <= kThreads;
 }
@@ -366,8 +483,9 @@ int default_tile(int M, int N, int cplx) {
     int best = 3;
     double bw = 1e30;
     int ba = 0;
-    for (int c = 1; c <= 5; ++c) {
+    for (int c = 1; c <= kTileCodes; ++c) {
         if (!tile_ok(c, M, N)) continue;
+        if (cplx && (c == 4 || c == 5)) continue;  // run as 4x4
         const int tm = kTile[c][0], tn = kTile[c][1];
         if (tm * tn * (cplx ? 2 : 1) > 32) continue;
         const double waste = (double)((M + tm - 1) / tm * tm) * ((N + tn - 1) / tn * tn) / ((double)M * N);
@@ -484,10 +602,20 @@ tsm_status tsm_batched_create(const tsm_batch_desc* d, int count, tsm_batch** ou
         int code = x.config & 0xFF;
         if (x.kind == TSM_KIND_TSMTTSM) {
             if (!tile_ok(code, x.M, x.N)) code = default_tile(x.M, x.N, in.cplx);
-        } else if (code < 1 || code > 3) {
-            code = x.N >= 16 ? 3 : (x.N >= 8 ? 2 : 1);
+        } else if (code < 1 || code > 4) {
+            // power-of-two threads per row when they cover N exactly, else
+            // any count (code 4)
+            const int tpr = x.N >= 16 ? 16 : (x.N >= 8 ? 8 : 4);
+            const int npt = (x.N + tpr - 1) / tpr;
+            const int cap = tpr == 4 ? 16 : (tpr == 8 ? 8 : 4);  // results per thread of codes 1, 2, 3
+            const bool exact = npt * tpr == x.N && npt <= cap && !(in.cplx && tpr == 4);  // complex code 1 is 8 x 8
+            code = exact ? (tpr == 16 ? 3 : (tpr == 8 ? 2 : 1)) : 4;
         }
         in.code = code;
+        if (x.kind == TSM_KIND_TSMM && code == 4) {
+            int npt = 1;
+            rt_tsmm_tpr(x.N, 4, &in.tpr, &npt);
+        }
         int64_t rows;
         const int lg = (x.config >> 8) & 0xFF;
         if (lg >= 10 && lg <= 22) {

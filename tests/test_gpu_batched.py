@@ -83,7 +83,7 @@ def test_batched_random_instances_and_replay(lib):
     assert items >= len(insts) and ctas >= 152
 
 
-@pytest.mark.parametrize("code", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("code", list(range(1, 13)))
 def test_batched_every_tsmttsm_tile_code(lib, code):
     import torch
     insts = [(0, c, M, N, 20000) for c in (False, True) for (M, N) in ((1, 1), (5, 7), (16, 16), (64, 64), (3, 64))]
@@ -95,10 +95,11 @@ def test_batched_every_tsmttsm_tile_code(lib, code):
         assert oracle.rel_fro(d[2].cpu().numpy(), _ref(kind, A, B, O, op, 0.5)) <= TOL, (code, cplx, M, N)
 
 
-@pytest.mark.parametrize("code", [1, 2, 3])
+@pytest.mark.parametrize("code", [1, 2, 3, 4])
 def test_batched_every_tsmm_code(lib, code):
     import torch
-    insts = [(1, c, M, N, 9000) for c in (False, True) for (M, N) in ((1, 1), (7, 5), (64, 64), (4, 64), (64, 4))]
+    insts = [(1, c, M, N, 9000) for c in (False, True)
+             for (M, N) in ((1, 1), (7, 5), (64, 64), (4, 64), (64, 4), (13, 39), (54, 17))]
     batch, host, dev = _build(insts, [code | (10 << 8)] * len(insts), beta=-1.0)
     batch.run()
     torch.cuda.synchronize()
