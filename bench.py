@@ -325,7 +325,11 @@ def run_ours(args, bw, bw_src):
     if world > 1:
         dist.barrier()
     total_ms = t_start.elapsed_time(t_end)
-    per_cfg = {cfg: statistics.mean(events[s][cfg][0].elapsed_time(events[s][cfg][1]) for s in range(args.steps))
+    # Per-call times are medians over the steps: the first call of the first
+    # timed step starts on an idle GPU and so also holds the host's launch
+    # latency (the whole-step value above keeps it).
+    per_cfg = {cfg: statistics.median(events[s][cfg][0].elapsed_time(events[s][cfg][1])
+                                      for s in range(args.steps))
                for cfg in SWEEP}
 
     ideal = {cfg: ideal_seconds(cfg[0], cfg[1], cfg[2], K, bw, p64) for cfg in SWEEP}
@@ -466,11 +470,15 @@ def run_e2e(args, flatA, flatB, outs, views, ideal, dev, K):
 # ------------------------------------------------------------------ extras
 
 def _time(fn, reps=3, warm=1):
+    """Mean milliseconds of `reps` calls, timed with CUDA events.  The start
+    event is recorded behind the warm-up calls (no synchronisation between),
+    so the timed calls find the host ahead of the GPU and their launch
+    latency is hidden, as in a stream of calls."""
     import torch
-    for _ in range(warm):
-        fn()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    for _ in range(max(warm, 1)):
+        fn()
     e0.record()
     for _ in range(reps):
         fn()
@@ -540,6 +548,59 @@ def run_tsmm_extra(flatA, flatB, K, bw, p64):
     return {"roofline_pct_whole_sweep": 100 * ideal / meas, "calls": out}
 
 
+def run_widths_extra(flatA, flatB, K, bw, p64):
+    """Every width: M = N = w for w = 1..64 at K = 2^24, real and complex,
+    TSMTTSM (op T real, op C complex) and TSMM with beta = 0 and beta = 1
+    (beta = 1 also reads B: 8cNK more bytes).  One warm-up call and one timed
+    call per point; percent of roofline per width and the widths below 90 %."""
+    import torch
+    import paper_1905_03136_gb300 as tsm
+    Bout = torch.empty(K * 128, dtype=torch.float64, device=flatA.device)
+    Bout.zero_()
+    res = {}
+    below = []
+    for kind in ("tsmttsm", "tsmm_beta0", "tsmm_beta1"):
+        res[kind] = {}
+        for cplx in (False, True):
+            c = 2 if cplx else 1
+            dt = torch.complex128 if cplx else torch.float64
+            pct, ms_list = [], []
+            for w in range(1, 65):
+                A = flatA[: K * w * c]
+                if cplx:
+                    A = A.view(torch.complex128)
+                A = A.view(K, w)
+                flops, nbytes = model(cplx, w, w, K)
+                if kind == "tsmttsm":
+                    Bm = flatB[: K * w * c]
+                    Bm = (Bm.view(torch.complex128) if cplx else Bm).view(K, w)
+                    C = torch.zeros((w, w), dtype=dt, device=flatA.device)
+                    ms = _time(lambda: tsm.tsmttsm(A, Bm, C, op="C" if cplx else "T"), reps=1)
+                else:
+                    beta = 0.0 if kind == "tsmm_beta0" else 1.0
+                    Cm = flatB[: w * w * c]
+                    Cm = (Cm.view(torch.complex128) if cplx else Cm).view(w, w)
+                    Bo = Bout[: K * w * c]
+                    Bo = (Bo.view(torch.complex128) if cplx else Bo).view(K, w)
+                    ms = _time(lambda: tsm.tsmm(A, Cm, Bo, 1.0, beta), reps=1)
+                    if beta != 0.0:
+                        nbytes += 8.0 * c * w * K
+                t_ideal = max(nbytes / (bw * 1e9), flops / (p64 * 1e9))
+                p = 100.0 * t_ideal / (ms * 1e-3)
+                pct.append(round(p, 1))
+                ms_list.append(round(ms, 4))
+                if p < 90.0:
+                    below.append("%s %s w=%d: %.1f" % (kind, "c64" if cplx else "r64", w, p))
+            res[kind]["c64" if cplx else "r64"] = {"roofline_pct": pct, "ms": ms_list,
+                                                   "min_pct": min(pct), "min_at_w": 1 + pct.index(min(pct))}
+    del Bout
+    torch.cuda.empty_cache()
+    res["what"] = ("M = N = w for w = 1..64 at K = 2^24: percent of roofline per width (index w - 1), "
+                   "TSMTTSM and TSMM (beta 0 / 1), real and complex")
+    res["below_90"] = below
+    return res
+
+
 GS_CASES = [(True, 32, 32), (True, 64, 64), (False, 64, 64), (False, 8, 8)]
 
 
@@ -583,7 +644,10 @@ def run_ramp_extra(flatA, flatB, bw, p64):
     the tuned TSMTTSM as K grows from 10^4 to 2^24.  `fixed_us` is the time
     of a call with one 16-row slab per CTA (K = 16 x grid): launch, the
     in-CTA and the cross-CTA reductions, and the epilogue, with almost no
-    streaming; `fixed_share` is that time over each call's time."""
+    streaming; `fixed_share` is that time over each call's time.  Calls are
+    timed back to back through the library's own timer (tsm_time_variant,
+    one warm-up call, then CUDA events around the repetitions), so that a
+    call of a few microseconds is not hidden behind Python's launch cost."""
     import torch
     import paper_1905_03136_gb300 as tsm
     res = []
@@ -593,13 +657,13 @@ def run_ramp_extra(flatA, flatB, bw, p64):
         var, grid = tsm.choose(tsm.KIND_TSMTTSM, dt, M, N, 1 << 20)
         k0 = 16 * max(grid, 1)
         A0, B0 = _views(flatA, flatB, cplx, M, N, k0)
-        fixed = _time(lambda: tsm.tsmttsm(A0, B0, C, op="C" if cplx else "T", variant=var, grid=grid), reps=20,
-                      warm=3)
+        fixed = tsm.time_variant(tsm.KIND_TSMTTSM, A0, B0, C, var, grid, reps=50)
         pts = []
         for K in RAMP_K:
             A, B = _views(flatA, flatB, cplx, M, N, K)
-            reps = 20 if K <= (1 << 22) else 2
-            ms = _time(lambda: tsm.tsmttsm(A, B, C, op="C" if cplx else "T"), reps=reps, warm=2)
+            v, g = tsm.choose(tsm.KIND_TSMTTSM, dt, M, N, K)
+            reps = 50 if K <= (1 << 22) else 3
+            ms = tsm.time_variant(tsm.KIND_TSMTTSM, A, B, C, v, g, reps=reps)
             t_ideal = ideal_seconds(cplx, M, N, K, bw, p64)
             pts.append({"K": K, "us": round(ms * 1e3, 2), "roofline_pct": round(100 * t_ideal / (ms * 1e-3), 2),
                         "fixed_share": round(fixed / ms, 4)})
@@ -760,6 +824,10 @@ def run_extras(args, flatA, flatB, K, bw, p64):
         ex["tsmm_sweep"] = run_tsmm_extra(flatA, flatB, K, bw, p64)
     except Exception as e:
         ex["tsmm_sweep"] = {"error": repr(e)}
+    try:
+        ex["widths"] = run_widths_extra(flatA, flatB, K, bw, p64)
+    except Exception as e:
+        ex["widths"] = {"error": repr(e)}
     try:
         ex["gs_step"] = run_gs_extra(flatA, flatB, K, bw, p64)
     except Exception as e:

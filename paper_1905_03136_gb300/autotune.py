@@ -10,6 +10,7 @@ before its built-in heuristic.
 
 Usage:
   python -m paper_1905_03136_gb300.autotune --K 16777216 --table T.txt --log L.jsonl [--kind tsmttsm|tsmm|both]
+         [--shapes r64:1x1,c64:2x2] [--keep-table]
 """
 
 import argparse
@@ -90,6 +91,8 @@ def main():
     ap.add_argument("--random", type=int, default=0,
                     help="tune this many random (dtype, M, N) shapes instead of the sweep")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--shapes", default=None,
+                    help="comma-separated shapes to tune instead of the sweep, e.g. r64:1x1,c64:2x2")
     ap.add_argument("--keep-table", action="store_true", help="merge into the loaded table")
     args = ap.parse_args()
     import torch
@@ -107,7 +110,13 @@ def main():
     import numpy as np
     rng = np.random.default_rng(args.seed)
     for kind in kinds:
-        if args.random:
+        if args.shapes:
+            shapes = []
+            for item in args.shapes.split(","):
+                dt, wh = item.split(":")
+                m, n = (int(x) for x in wh.split("x"))
+                shapes.append((dt == "c64", m, n))
+        elif args.random:
             shapes = [(bool(rng.integers(0, 2)), int(rng.integers(1, 65)), int(rng.integers(1, 65)))
                       for _ in range(args.random)]
         else:

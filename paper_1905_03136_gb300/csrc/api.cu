@@ -113,6 +113,7 @@ struct Registry {
         register_fp64_variants(tsmttsm, tsmm);
         register_generated_variants(tsmttsm, tsmm);
         register_rt_variants(tsmttsm, tsmm);
+        register_narrow_variants(tsmttsm, tsmm);
     }
 };
 

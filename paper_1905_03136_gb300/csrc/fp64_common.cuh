@@ -30,6 +30,113 @@ __device__ __forceinline__ void sum_partials(const double* ws, int MNc, int o, i
                  ((acc[c][4] + acc[c][5]) + (acc[c][6] + acc[c][7]));
 }
 
+// Warp-level sum of V values per lane (V a power of two, 1 <= V <= 32) by
+// recursive halving: at the step with lane offset o = 16, 8, ..., a lane
+// keeps half of its remaining values (the upper half if its bit o is set)
+// and adds its partner's copy of that half, so a step costs as many adds
+// as values remain, V - 1 adds over the first log2(V) steps; the remaining
+// steps add the single value across lanes (butterfly).  On return v[0] of
+// lane l holds the warp total of value l >> (5 - log2 V), and all lanes with
+// the same l >> (5 - log2 V) hold identical bits.  A plain butterfly per
+// value would take 5 V adds; on a part whose FP64 pipe issues one warp
+// instruction per 64 cycles per scheduler, the difference is the fixed cost
+// of the in-CTA reduction.  Pairing is fixed, so results repeat bit for bit.
+template <int V>
+__device__ __forceinline__ void warp_reduce_scatter(double* v, int lane) {
+    static_assert(V >= 1 && V <= 32 && (V & (V - 1)) == 0, "V must be a power of two <= 32");
+    int n = V;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool up = (lane & o) != 0;
+        if (n > 1) {
+            const int h = n >> 1;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                if (i >= h) break;
+                const double send = up ? v[i] : v[h + i];
+                const double keep = up ? v[h + i] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+            n = h;
+        } else {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+        }
+    }
+}
+
+constexpr int log2_pow2(int v) { return v <= 1 ? 0 : 1 + log2_pow2(v >> 1); }
+constexpr int next_pow2(int v) { return v <= 1 ? 1 : 2 * next_pow2((v + 1) >> 1); }
+
+// Cross-CTA step of the TSMTTSM reduction, called by every thread of every
+// CTA once its M x N partial is in the workspace (a.ws + blockIdx.x * M*N*CC):
+// the last CTA to take the ticket sums all partials (S threads share each
+// entry, thread s taking CTAs s, s + S, ... in order; the S slice sums are
+// combined by a pairwise tree with a fixed pairing), stores alpha * sum + beta * C (C not read when
+// beta == 0) and resets the ticket for the next launch.  `red` is shared
+// memory of at least kBlock * CC doubles, free for reuse.
+template <int CC>
+__device__ __forceinline__ void tsmttsm_cross_cta(const TsmttsmArgs& a, double* red) {
+    __shared__ unsigned s_last;
+    const int M = a.M, N = a.N;
+    const int t = threadIdx.x;
+    const int MNc = M * N * CC;
+    __threadfence();
+    __syncthreads();
+    if (t == 0) s_last = (atomicAdd(a.ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int MN = M * N;
+    const int G = gridDim.x;
+    // S threads per entry when there are fewer entries than threads.
+    int S = 1;
+    while (S * 2 * MN <= (int)blockDim.x && S * 2 <= G) S *= 2;
+    for (int base = 0; base < MN * S; base += blockDim.x) {
+        const int w = base + t;
+        double v[CC];
+        const bool mine = w < MN * S;
+        if (mine) sum_partials<CC>(a.ws, MNc, w / S, G, w % S, S, v);
+        if (S > 1) {
+            // slice sums of one entry are adjacent threads: pairwise tree
+            // with a fixed pairing (slice s absorbs slice s + h).  A serial
+            // chain of S - 1 dependent adds would cost S - 1 full FP64
+            // issue slots of this part's slow FP64 pipe.
+#pragma unroll
+            for (int c = 0; c < CC; ++c) red[t * CC + c] = mine ? v[c] : 0.0;
+            __syncthreads();
+            for (int h = S >> 1; h >= 1; h >>= 1) {
+                if (mine && (w % S) < h)
+#pragma unroll
+                    for (int c = 0; c < CC; ++c) red[t * CC + c] += red[(t + h) * CC + c];
+                __syncthreads();
+            }
+#pragma unroll
+            for (int c = 0; c < CC; ++c) v[c] = red[t * CC + c];
+            __syncthreads();
+        }
+        if (!mine || (w % S) != 0) continue;
+        const int o = w / S;
+        const int m = o / N, n = o - m * N;
+        double* out = a.C + ((int64_t)m * a.ldc + n) * CC;
+        if (CC == 1) {
+            double r = a.alpha_r * v[0];
+            if (!a.beta_zero) r = fma(a.beta_r, out[0], r);
+            out[0] = r;
+        } else {
+            double rr = a.alpha_r * v[0] - a.alpha_i * v[CC - 1];
+            double ri = a.alpha_r * v[CC - 1] + a.alpha_i * v[0];
+            if (!a.beta_zero) {
+                const double orr = out[0], oi = out[CC - 1];
+                rr += a.beta_r * orr - a.beta_i * oi;
+                ri += a.beta_r * oi + a.beta_i * orr;
+            }
+            out[0] = rr;
+            out[CC - 1] = ri;
+        }
+    }
+    if (t == 0) *a.ticket = 0u;
+}
+
 // Deterministic two-level reduction of TSMTTSM partial tiles (replaces the
 // atomics of Sec. 3.2).  Thread (lane, p) holds acc[(i * TN + j) * CC + c] for
 // C[pm + i*PM][pn + j*PN] with pm = p % PM, pn = p / PM.
@@ -38,7 +145,7 @@ __device__ __forceinline__ void sum_partials(const double* ws, int MNc, int o, i
 //      tile entry at a time, into this CTA's M x N partial in the workspace;
 //   2. the last CTA to take the ticket sums all partials: S threads share
 //      each entry, thread s taking CTAs s, s + S, ... in order, and the S
-//      slice sums are added in slice order; then alpha * sum + beta * C (C
+//      slice sums are combined by a fixed pairwise tree; then alpha * sum + beta * C (C
 //      not read when beta == 0) is stored and the ticket reset for the next
 //      launch.
 // Every order above depends only on (G, M, N, tile), so results repeat bit
@@ -49,7 +156,6 @@ template <int TM, int TN, int CC>
 __device__ __forceinline__ void tsmttsm_finish(const TsmttsmArgs& a, const double* acc, int PM, int PN,
                                                int L, int lane, int p, bool active, int tm = TM, int tn = TN) {
     __shared__ double red[kBlock * CC];
-    __shared__ unsigned s_last;
     const int M = a.M, N = a.N;
     const int P = PM * PN;
     const int t = threadIdx.x;
@@ -77,54 +183,7 @@ __device__ __forceinline__ void tsmttsm_finish(const TsmttsmArgs& a, const doubl
                 __syncthreads();
             }
 
-    __threadfence();
-    __syncthreads();
-    if (t == 0) s_last = (atomicAdd(a.ticket, 1u) == gridDim.x - 1);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    const int MN = M * N;
-    const int G = gridDim.x;
-    // S threads per entry when there are fewer entries than threads.
-    int S = 1;
-    while (S * 2 * MN <= (int)blockDim.x && S * 2 <= G) S *= 2;
-    for (int base = 0; base < MN * S; base += blockDim.x) {
-        const int w = base + t;
-        double v[CC];
-        const bool mine = w < MN * S;
-        if (mine) sum_partials<CC>(a.ws, MNc, w / S, G, w % S, S, v);
-        if (S > 1) {
-            // slice sums of one entry are adjacent threads: combine in order
-#pragma unroll
-            for (int c = 0; c < CC; ++c) red[t * CC + c] = mine ? v[c] : 0.0;
-            __syncthreads();
-            if (mine && (w % S) == 0)
-                for (int s = 1; s < S; ++s)
-#pragma unroll
-                    for (int c = 0; c < CC; ++c) v[c] += red[(t + s) * CC + c];
-            __syncthreads();
-        }
-        if (!mine || (w % S) != 0) continue;
-        const int o = w / S;
-        const int m = o / N, n = o - m * N;
-        double* out = a.C + ((int64_t)m * a.ldc + n) * CC;
-        if (CC == 1) {
-            double r = a.alpha_r * v[0];
-            if (!a.beta_zero) r = fma(a.beta_r, out[0], r);
-            out[0] = r;
-        } else {
-            double rr = a.alpha_r * v[0] - a.alpha_i * v[CC - 1];
-            double ri = a.alpha_r * v[CC - 1] + a.alpha_i * v[0];
-            if (!a.beta_zero) {
-                const double orr = out[0], oi = out[CC - 1];
-                rr += a.beta_r * orr - a.beta_i * oi;
-                ri += a.beta_r * oi + a.beta_i * orr;
-            }
-            out[0] = rr;
-            out[CC - 1] = ri;
-        }
-    }
-    if (t == 0) *a.ticket = 0u;
+    tsmttsm_cross_cta<CC>(a, red);
 }
 
 // TSMM output store: B[row][n] = acc (+ beta * B[row][n] unless beta == 0).

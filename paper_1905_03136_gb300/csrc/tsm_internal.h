@@ -60,6 +60,7 @@ struct Variant {
 void register_fp64_variants(std::vector<Variant>& tsmttsm, std::vector<Variant>& tsmm);
 void register_generated_variants(std::vector<Variant>& tsmttsm, std::vector<Variant>& tsmm);
 void register_rt_variants(std::vector<Variant>& tsmttsm, std::vector<Variant>& tsmm);
+void register_narrow_variants(std::vector<Variant>& tsmttsm, std::vector<Variant>& tsmm);
 
 // Per-launch choice of the runtime-threads-per-row TSMM variants (kernels_rt.cu).
 void rt_tsmm_tpr(int N, int nptmax, int* tpr, int* npt);

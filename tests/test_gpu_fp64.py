@@ -46,9 +46,9 @@ def _variants_for(tsm, kind, dt, M, N):
     return [i for i in range(lib.tsm_variant_count(kind)) if lib.tsm_variant_supports(kind, i, dt, M, N)]
 
 
-TSMTTSM_SHAPES = [(1, 1), (2, 2), (2, 3), (4, 4), (7, 5), (8, 8), (16, 16), (33, 17), (32, 32), (64, 64),
+TSMTTSM_SHAPES = [(1, 1), (2, 2), (2, 3), (3, 3), (4, 4), (7, 5), (8, 8), (16, 16), (33, 17), (32, 32), (64, 64),
                   (1, 64), (64, 1), (8, 32), (32, 8), (13, 64), (49, 25)]
-TSMM_SHAPES = [(1, 1), (2, 2), (3, 5), (4, 4), (8, 8), (16, 16), (31, 7), (32, 32), (64, 64), (4, 64),
+TSMM_SHAPES = [(1, 1), (2, 2), (3, 3), (3, 5), (4, 4), (8, 8), (16, 16), (31, 7), (32, 32), (64, 64), (4, 64),
                (64, 4), (1, 64), (64, 1), (54, 17), (28, 39)]
 
 
@@ -191,6 +191,87 @@ def test_tsmm_integer_bitwise_identity_and_ld(tsm, cplx):
     oracle.tsmm(M, N, K, 1.0, A2, lda, C2, ldc, 0.0, ref2, N)
     assert oracle.rel_fro(got[:, :N], ref2) <= TOL
     assert np.all(np.isnan(got[:, N:]))
+
+
+NARROW = [(False, 1, 1), (False, 2, 2), (False, 3, 3), (False, 4, 4), (True, 1, 1), (True, 2, 2)]
+
+
+def _narrow(tsm, kind, cplx, M, N):
+    pre = "%s_%s_narrow_m%dn%d_" % ("tsmttsm" if kind == tsm.KIND_TSMTTSM else "tsmm", "c64" if cplx else "r64", M, N)
+    vs = [v["index"] for v in tsm.variants(kind) if v["name"].startswith(pre)]
+    assert len(vs) == 5, pre
+    return vs
+
+
+@pytest.mark.parametrize("case", NARROW, ids=lambda c: "%s%dx%d" % ("c64_" if c[0] else "r64_", c[1], c[2]))
+def test_narrow_variants_every_layout(tsm, case):
+    """The vector-streaming narrow kernels on every layout they meet: rows
+    stored without padding and vector-aligned (vector path), a base pointer
+    one element off the vector boundary and a padded leading dimension (both
+    the scalar row path), with row counts that leave a ragged group at the
+    end and grids from 1 CTA to more CTAs than groups."""
+    cplx, M, N = case
+    dt = np.complex128 if cplx else np.float64
+    ops = ("T", "C") if cplx else ("T",)
+    for K in (4099, 1, 3, 37):
+        A = synth.block_vector(61, K + 1, M + 1, complex_=cplx)
+        B = synth.block_vector(62, K + 1, N + 1, complex_=cplx)
+        Cm = synth.small_matrix(63, M, N, complex_=cplx)
+        B0 = synth.block_vector(64, K + 1, N + 1, complex_=cplx)
+        dA_pad, dB_pad = dev(A), dev(B)
+        flatA = dev(np.concatenate([np.zeros(1, dt), np.ascontiguousarray(A[:K, :M]).ravel()]))
+        flatB = dev(np.concatenate([np.zeros(1, dt), np.ascontiguousarray(B[:K, :N]).ravel()]))
+        views = {
+            "packed": (dev(A[:K, :M]), dev(B[:K, :N])),
+            "offset": (flatA[1:].view(K, M), flatB[1:].view(K, N)),
+            "padded": (dA_pad[:K, :M], dB_pad[:K, :N]),
+        }
+        for op in ops:
+            ref = oracle.gram(A[:K, :M], B[:K, :N], op)
+            for lay, (a, b) in views.items():
+                for v in _narrow(tsm, tsm.KIND_TSMTTSM, cplx, M, N):
+                    for grid in (0, 1, 5, 400):
+                        C = host(tsm.tsmttsm(a, b, op=op, variant=v, grid=grid))
+                        err = oracle.rel_fro(C, ref)
+                        assert err <= TOL, (tsm.variants(tsm.KIND_TSMTTSM)[v]["name"], K, lay, op, grid, err)
+        # TSMM: B = A C and B = alpha A C + beta B on the same layouts
+        alpha, beta = (0.75 - 0.5j, 1.0 - 2.0j) if cplx else (0.75, -2.0)
+        ref0 = oracle.apply(A[:K, :M], Cm)
+        ref1 = oracle.apply(A[:K, :M], Cm, alpha, beta, B0[:K, :N])
+        dC = dev(Cm)
+        for lay in ("packed", "offset", "padded"):
+            a = views[lay][0]
+            for v in _narrow(tsm, tsm.KIND_TSMM, cplx, M, N):
+                for grid in (0, 1, 5, 400):
+                    if lay == "padded":
+                        outbuf = dev(np.full((K + 1, N + 1), np.nan, dtype=dt))
+                        out = outbuf[:K, :N]
+                    elif lay == "offset":
+                        outbuf = dev(np.full(K * N + 1, np.nan, dtype=dt))
+                        out = outbuf[1:].view(K, N)
+                    else:
+                        outbuf = dev(np.full((K, N), np.nan, dtype=dt))
+                        out = outbuf
+                    tsm.tsmm(a, dC, out, variant=v, grid=grid)
+                    got = host(out)
+                    assert oracle.rel_fro(got, ref0) <= TOL, (tsm.variants(tsm.KIND_TSMM)[v]["name"], K, lay, grid)
+                    if lay == "padded":
+                        assert np.all(np.isnan(host(outbuf)[:, N:])), "padding of B written"
+                    if lay == "offset":
+                        assert np.isnan(host(outbuf)[0]), "element before B written"
+                # beta != 0 reads B
+                if lay == "padded":
+                    ob = dev(B0)
+                    out = ob[:K, :N]
+                elif lay == "offset":
+                    ob = dev(np.concatenate([np.zeros(1, dt), np.ascontiguousarray(B0[:K, :N]).ravel()]))
+                    out = ob[1:].view(K, N)
+                else:
+                    ob = dev(np.ascontiguousarray(B0[:K, :N]))
+                    out = ob
+                tsm.tsmm(a, dC, out, alpha, beta, variant=v)
+                err = oracle.rel_fro(host(out), ref1)
+                assert err <= TOL, (tsm.variants(tsm.KIND_TSMM)[v]["name"], K, lay, "beta", err)
 
 
 def test_device_fill_matches_host_generator(tsm):
