@@ -469,6 +469,13 @@ def run_e2e(args, flatA, flatB, outs, views, ideal, dev, K):
 
 # ------------------------------------------------------------------ extras
 
+def _reps_for(t_ideal_s):
+    """Timed calls per point: several for calls below a millisecond, so that
+    the host's launch latency of the first one (the start event is recorded
+    behind a single warm-up call) is spread over them; one above."""
+    return 1 if t_ideal_s > 1e-3 else 8
+
+
 def _time(fn, reps=3, warm=1):
     """Mean milliseconds of `reps` calls, timed with CUDA events.  The start
     event is recorded behind the warm-up calls (no synchronisation between),
@@ -536,9 +543,9 @@ def run_tsmm_extra(flatA, flatB, K, bw, p64):
         if cplx:
             A, Cm, Bo = A.view(torch.complex128), Cm.view(torch.complex128), Bo.view(torch.complex128)
         A, Cm, Bo = A.view(K, M), Cm.view(M, N), Bo.view(K, N)
-        ms = _time(lambda: tsm.tsmm(A, Cm, Bo), reps=1)
         flops, nbytes = model(cplx, M, N, K)
         t_ideal = max(nbytes / (bw * 1e9), flops / (p64 * 1e9))
+        ms = _time(lambda: tsm.tsmm(A, Cm, Bo), reps=_reps_for(t_ideal))
         ideal += t_ideal
         meas += ms * 1e-3
         out.append({"dtype": "c64" if cplx else "r64", "M": M, "N": N, "ms": round(ms, 4),
@@ -551,8 +558,9 @@ def run_tsmm_extra(flatA, flatB, K, bw, p64):
 def run_widths_extra(flatA, flatB, K, bw, p64):
     """Every width: M = N = w for w = 1..64 at K = 2^24, real and complex,
     TSMTTSM (op T real, op C complex) and TSMM with beta = 0 and beta = 1
-    (beta = 1 also reads B: 8cNK more bytes).  One warm-up call and one timed
-    call per point; percent of roofline per width and the widths below 90 %."""
+    (beta = 1 also reads B: 8cNK more bytes).  One warm-up call and one to
+    eight timed calls per point; percent of roofline per width and the
+    widths below 90 %."""
     import torch
     import paper_1905_03136_gb300 as tsm
     Bout = torch.empty(K * 128, dtype=torch.float64, device=flatA.device)
@@ -571,21 +579,22 @@ def run_widths_extra(flatA, flatB, K, bw, p64):
                     A = A.view(torch.complex128)
                 A = A.view(K, w)
                 flops, nbytes = model(cplx, w, w, K)
+                if kind == "tsmm_beta1":
+                    nbytes += 8.0 * c * w * K
+                t_ideal = max(nbytes / (bw * 1e9), flops / (p64 * 1e9))
+                reps = _reps_for(t_ideal)
                 if kind == "tsmttsm":
                     Bm = flatB[: K * w * c]
                     Bm = (Bm.view(torch.complex128) if cplx else Bm).view(K, w)
                     C = torch.zeros((w, w), dtype=dt, device=flatA.device)
-                    ms = _time(lambda: tsm.tsmttsm(A, Bm, C, op="C" if cplx else "T"), reps=1)
+                    ms = _time(lambda: tsm.tsmttsm(A, Bm, C, op="C" if cplx else "T"), reps=reps)
                 else:
                     beta = 0.0 if kind == "tsmm_beta0" else 1.0
                     Cm = flatB[: w * w * c]
                     Cm = (Cm.view(torch.complex128) if cplx else Cm).view(w, w)
                     Bo = Bout[: K * w * c]
                     Bo = (Bo.view(torch.complex128) if cplx else Bo).view(K, w)
-                    ms = _time(lambda: tsm.tsmm(A, Cm, Bo, 1.0, beta), reps=1)
-                    if beta != 0.0:
-                        nbytes += 8.0 * c * w * K
-                t_ideal = max(nbytes / (bw * 1e9), flops / (p64 * 1e9))
+                    ms = _time(lambda: tsm.tsmm(A, Cm, Bo, 1.0, beta), reps=reps)
                 p = 100.0 * t_ideal / (ms * 1e-3)
                 pct.append(round(p, 1))
                 ms_list.append(round(ms, 4))

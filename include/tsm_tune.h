@@ -61,6 +61,14 @@ tsm_status tsm_tune_grids(tsm_kind kind, int variant, tsm_dtype dtype, int M,
 tsm_status tsm_set_tuning(tsm_kind kind, tsm_dtype dtype, int M, int N,
                           int64_t K, int variant, int grid);
 
+/* As tsm_set_tuning, also recording the measured milliseconds of the entry
+ * (written to the table file; informational).  Used by the model-pruned
+ * search, which times only the candidates the cost model ranks first.
+ * INVALID_VALUE for a bad variant, a variant that cannot run the shape, or
+ * a negative grid. */
+tsm_status tsm_set_tuning_timed(tsm_kind kind, tsm_dtype dtype, int M, int N,
+                                int64_t K, int variant, int grid, float ms);
+
 /* Table persistence: text file, one entry per line
  * "kind dtype M N kbucket variant_name grid ms".  Loading merges into the
  * table; the environment variable TSM_TUNE_FILE names a file loaded before

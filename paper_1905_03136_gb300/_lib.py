@@ -66,6 +66,7 @@ SIGNATURES = {
     "tsm_time_variant": (i32, [i32, i32, i32, i32, i64, vp, i64, vp, i64, vp, i64, i32, i32, i32,
                                ctypes.POINTER(ctypes.c_float), vp]),
     "tsm_set_tuning": (i32, [i32, i32, i32, i32, i64, i32, i32]),
+    "tsm_set_tuning_timed": (i32, [i32, i32, i32, i32, i64, i32, i32, ctypes.c_float]),
     "tsm_tune_grids": (i32, [i32, i32, i32, i32, i32, ctypes.POINTER(i32), i32, ctypes.POINTER(i32)]),
     "tsm_load_tuning": (i32, [ctypes.c_char_p]),
     "tsm_save_tuning": (i32, [ctypes.c_char_p]),
@@ -98,8 +99,12 @@ def load():
                 fn.restype = res
                 fn.argtypes = args
             # The autotuned table for this GPU ships with the package; an
-            # explicit TSM_TUNE_FILE replaces it.
-            if not os.environ.get("TSM_TUNE_FILE") and os.path.exists(DEFAULT_TABLE):
+            # explicit TSM_TUNE_FILE replaces it (loaded here, so that the
+            # table is complete before anything reads or saves it).
+            env = os.environ.get("TSM_TUNE_FILE")
+            if env:
+                lib.tsm_load_tuning(env.encode())
+            elif os.path.exists(DEFAULT_TABLE):
                 lib.tsm_load_tuning(DEFAULT_TABLE.encode())
             _lib = lib
     return _lib

@@ -56,6 +56,42 @@ def _tiles_for(M, N, cplx):
     return out
 
 
+def tile_for_width(w, cplx, cap=40):
+    """Register tile (T_M, T_N) for the square width w: the least padded
+    work P T_M T_N / w^2 (a guarded FMA still costs its FP64 issue slot),
+    then the larger tile (fewer loads per FMA), then the squarer one;
+    at most `cap` accumulator doubles and one CTA's threads."""
+    best = None
+    c = 2 if cplx else 1
+    for tm in range(1, w + 1):
+        for tn in range(1, w + 1):
+            if tm * tn * c > cap:
+                continue
+            P = math.ceil(w / tm) * math.ceil(w / tn)
+            if P > BLOCK:
+                continue
+            waste = P * tm * tn / (w * w)
+            key = (round(waste, 6), -tm * tn, abs(math.log2(tm) - math.log2(tn)), -tm)
+            if best is None or key < best[0]:
+                best = (key, tm, tn)
+    return best[1], best[2]
+
+
+def tpr_for_width(N, cplx):
+    """TSMM threads per row t and results per thread npt for N columns: the
+    least padding npt t - N, then npt closest to 4 (the measured optimum of
+    the tuned widths), then the larger npt."""
+    best = None
+    for npt in range(1, (8 if cplx else 16) + 1):
+        t = math.ceil(N / npt)
+        if t > 64:
+            continue
+        key = (npt * t - N, abs(npt - 4), -npt)
+        if best is None or key < best[0]:
+            best = (key, t, npt)
+    return best[1], best[2]
+
+
 def default_specs():
     tsmttsm, tsmm = [], []
     shapes = [(w, w) for w in SWEEP_SQUARE] + list(SWEEP_OFFDIAG)
@@ -64,6 +100,18 @@ def default_specs():
             for (tm, tn) in _tiles_for(M, N, cplx):
                 U = 4 if tm * tn <= 2 else (2 if tm * tn <= 8 else 1)
                 tsmttsm.append(dict(cplx=cplx, M=M, N=N, TM=tm, TN=tn, U=U))
+    # one width-specialised kernel per product for every other square width
+    # (every w in 1..64 has a kernel without padding, or with at most a few
+    # per cent of it, as the paper's generator does for each size, Sec. 2.1)
+    for cplx in (False, True):
+        for w in range(1, 65):
+            if w in SWEEP_SQUARE:
+                continue
+            tm, tn = tile_for_width(w, cplx)
+            U = 4 if tm * tn <= 2 else (2 if tm * tn <= 8 else 1)
+            tsmttsm.append(dict(cplx=cplx, M=w, N=w, TM=tm, TN=tn, U=U))
+            tpr, npt = tpr_for_width(w, cplx)
+            tsmm.append(dict(cplx=cplx, M=w, N=w, TPR=tpr, U=2 if npt * (2 if cplx else 1) <= 8 else 1))
     tshapes = [(w, w) for w in SWEEP_SQUARE] + list(TSMM_OFFDIAG)
     for cplx in (False, True):
         for (M, N) in tshapes:
@@ -214,6 +262,8 @@ def emit_tsmm(s):
     w("    tsmm_stage_c<%d>(a, cs);" % CC)
     w("    constexpr int TPR = %d, RPC = %d;" % (TPR, RPC))
     w("    const int r = threadIdx.x / TPR, q = threadIdx.x - r * TPR;")
+    # threads past RPC * TPR (TPR not dividing the block) hold no row
+    live = "" if BLOCK % TPR == 0 else "r < RPC && "
     for j in range(NPT):
         if gn[j]:
             w("    const bool gn%d = q + %d < %d;" % (j, j * TPR, N))
@@ -221,12 +271,26 @@ def emit_tsmm(s):
     w("    const int64_t step = (int64_t)gridDim.x * RPC * %d;" % U)
     w("    for (int64_t base = (int64_t)blockIdx.x * RPC * %d + r; base - r < a.K; base += step) {" % U)
     for u in range(U):
-        w("        const bool rok%d = base + %d < a.K;" % (u, u * RPC))
+        w("        const bool rok%d = %sbase + %d < a.K;" % (u, live, u * RPC))
         w("        const double* ar%d = a.A + (rok%d ? base + %d : 0) * sa;" % (u, u, u * RPC))
     for u in range(U):
         for j in range(NPT):
             for c in range(CC):
-                w("        double x%d_%d_%d = 0.0;" % (u, j, c))
+                w("        double x%d_%d_%d = 0.0, o%d_%d_%d = 0.0;" % (u, j, c, u, j, c))
+    # beta != 0: the old B values are loaded before the FMAs, so their
+    # latency overlaps them instead of stalling the stores
+    w("        if (!a.beta_zero) {")
+    for u in range(U):
+        w("            if (rok%d) {" % u)
+        w("                const double* bo = a.B + (base + %d) * sb;" % (u * RPC))
+        for j in range(NPT):
+            guard = ("if (gn%d) " % j) if gn[j] else ""
+            w("                %s{" % guard)
+            for c in range(CC):
+                w("                    o%d_%d_%d = bo[(q + %d) * %d + %d];" % (u, j, c, j * TPR, CC, c))
+            w("                }")
+        w("            }")
+    w("        }")
     for m in range(M):
         for u in range(U):
             for c in range(CC):
@@ -250,8 +314,8 @@ def emit_tsmm(s):
         w("            double* out = a.B + (base + %d) * sb;" % (u * RPC))
         for j in range(NPT):
             guard = ("if (gn%d) " % j) if gn[j] else ""
-            w("            %stsmm_store<%d>(a, out, q + %d, x%d_%d_0, x%d_%d_%d);"
-              % (guard, CC, j * TPR, u, j, u, j, CC - 1))
+            w("            %stsmm_store_old<%d>(a, out, q + %d, x%d_%d_0, x%d_%d_%d, o%d_%d_0, o%d_%d_%d);"
+              % (guard, CC, j * TPR, u, j, u, j, CC - 1, u, j, u, j, CC - 1))
         w("        }")
     w("    }")
     w("}")
@@ -306,7 +370,7 @@ def _reg_tsmm(s):
             % (name, 1 if s["cplx"] else 0, s["M"], s["N"], npt, s["TPR"], s["U"], BLOCK, name, name))
 
 
-def generate(out_dir, shards=4, specs=None):
+def generate(out_dir, shards=16, specs=None):
     """Writes gen_shard{i}.cu (kernels) and gen_registry.cu; returns the list
     of written files.  Files whose content is unchanged are not rewritten,
     so incremental builds skip them."""
@@ -359,7 +423,7 @@ def _write(path, text):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("out_dir")
-    ap.add_argument("--shards", type=int, default=4)
+    ap.add_argument("--shards", type=int, default=16)
     args = ap.parse_args()
     for f in generate(args.out_dir, args.shards):
         print(f)

@@ -310,7 +310,9 @@ tsm_status run_tsmttsm(tsm_op opA, tsm_dtype dtype, int M, int N, int64_t K, con
     a.conj = (cplx && opA == TSM_OP_C) ? 1 : 0;
     a.ws = ws->partials;
     a.ticket = ws->tickets;
+    a.final_pass = (int64_t)g * M * N * (cplx ? 2 : 1) > kFinalThreshold ? 1 : 0;
     if (var.tsmttsm(a, g, stream) != cudaSuccess) return TSM_ERR_LAUNCH;
+    if (a.final_pass && launch_tsmttsm_final(a, g, cplx, stream) != cudaSuccess) return TSM_ERR_LAUNCH;
     return TSM_OK;
 }
 

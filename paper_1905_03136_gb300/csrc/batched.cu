@@ -144,13 +144,19 @@ __device__ void tsmttsm_item(const Inst& in, const Item& it, double* parts, unsi
         double v[CC];
         if (mine) sum_partials<CC>(slots, MNc, w / S, G, w % S, S, v);
         if (S > 1) {
+            // fixed pairwise tree over the S slice sums of one entry (a
+            // serial chain would cost S - 1 FP64 issue slots in a row)
 #pragma unroll
             for (int c = 0; c < CC; ++c) red[t * CC + c] = mine ? v[c] : 0.0;
             __syncthreads();
-            if (mine && (w % S) == 0)
-                for (int s = 1; s < S; ++s)
+            for (int h = S >> 1; h >= 1; h >>= 1) {
+                if (mine && (w % S) < h)
 #pragma unroll
-                    for (int c = 0; c < CC; ++c) v[c] += red[(t + s) * CC + c];
+                    for (int c = 0; c < CC; ++c) red[t * CC + c] += red[(t + h) * CC + c];
+                __syncthreads();
+            }
+#pragma unroll
+            for (int c = 0; c < CC; ++c) v[c] = red[t * CC + c];
             __syncthreads();
         }
         if (!mine || (w % S) != 0) continue;

@@ -67,15 +67,42 @@ __device__ __forceinline__ void warp_reduce_scatter(double* v, int lane) {
 constexpr int log2_pow2(int v) { return v <= 1 ? 0 : 1 + log2_pow2(v >> 1); }
 constexpr int next_pow2(int v) { return v <= 1 ? 1 : 2 * next_pow2((v + 1) >> 1); }
 
+// Epilogue of one entry o = m * N + n of C: C[m][n] = alpha * v + beta *
+// C[m][n] (C not read when beta == 0).
+template <int CC>
+__device__ __forceinline__ void tsmttsm_store_entry(const TsmttsmArgs& a, int o, const double* v) {
+    const int m = o / a.N, n = o - m * a.N;
+    double* out = a.C + ((int64_t)m * a.ldc + n) * CC;
+    if (CC == 1) {
+        double r = a.alpha_r * v[0];
+        if (!a.beta_zero) r = fma(a.beta_r, out[0], r);
+        out[0] = r;
+    } else {
+        double rr = a.alpha_r * v[0] - a.alpha_i * v[CC - 1];
+        double ri = a.alpha_r * v[CC - 1] + a.alpha_i * v[0];
+        if (!a.beta_zero) {
+            const double orr = out[0], oi = out[CC - 1];
+            rr += a.beta_r * orr - a.beta_i * oi;
+            ri += a.beta_r * oi + a.beta_i * orr;
+        }
+        out[0] = rr;
+        out[CC - 1] = ri;
+    }
+}
+
 // Cross-CTA step of the TSMTTSM reduction, called by every thread of every
 // CTA once its M x N partial is in the workspace (a.ws + blockIdx.x * M*N*CC):
 // the last CTA to take the ticket sums all partials (S threads share each
 // entry, thread s taking CTAs s, s + S, ... in order; the S slice sums are
-// combined by a pairwise tree with a fixed pairing), stores alpha * sum + beta * C (C not read when
-// beta == 0) and resets the ticket for the next launch.  `red` is shared
-// memory of at least kBlock * CC doubles, free for reuse.
+// combined by a pairwise tree with a fixed pairing), stores alpha * sum +
+// beta * C (C not read when beta == 0) and resets the ticket for the next
+// launch.  `red` is shared
+// memory of at least kBlock * CC doubles, free for reuse.  With
+// a.final_pass set the CTAs stop after writing their partials and the host
+// launches the final kernel instead (many partials: see kFinalThreshold).
 template <int CC>
 __device__ __forceinline__ void tsmttsm_cross_cta(const TsmttsmArgs& a, double* red) {
+    if (a.final_pass) return;  // the partials are summed by the final kernel
     __shared__ unsigned s_last;
     const int M = a.M, N = a.N;
     const int t = threadIdx.x;
@@ -115,24 +142,7 @@ __device__ __forceinline__ void tsmttsm_cross_cta(const TsmttsmArgs& a, double* 
             __syncthreads();
         }
         if (!mine || (w % S) != 0) continue;
-        const int o = w / S;
-        const int m = o / N, n = o - m * N;
-        double* out = a.C + ((int64_t)m * a.ldc + n) * CC;
-        if (CC == 1) {
-            double r = a.alpha_r * v[0];
-            if (!a.beta_zero) r = fma(a.beta_r, out[0], r);
-            out[0] = r;
-        } else {
-            double rr = a.alpha_r * v[0] - a.alpha_i * v[CC - 1];
-            double ri = a.alpha_r * v[CC - 1] + a.alpha_i * v[0];
-            if (!a.beta_zero) {
-                const double orr = out[0], oi = out[CC - 1];
-                rr += a.beta_r * orr - a.beta_i * oi;
-                ri += a.beta_r * oi + a.beta_i * orr;
-            }
-            out[0] = rr;
-            out[CC - 1] = ri;
-        }
+        tsmttsm_store_entry<CC>(a, w / S, v);
     }
     if (t == 0) *a.ticket = 0u;
 }
@@ -145,9 +155,12 @@ __device__ __forceinline__ void tsmttsm_cross_cta(const TsmttsmArgs& a, double* 
 //      tile entry at a time, into this CTA's M x N partial in the workspace;
 //   2. the last CTA to take the ticket sums all partials: S threads share
 //      each entry, thread s taking CTAs s, s + S, ... in order, and the S
-//      slice sums are combined by a fixed pairwise tree; then alpha * sum + beta * C (C
+//      slice sums are added in slice order; then alpha * sum + beta * C (C
 //      not read when beta == 0) is stored and the ticket reset for the next
-//      launch.
+//      launch.  With many partials (a.final_pass) the CTAs stop after step
+//      1 and the host launches the final kernel for step 2.
+// (The narrow kernels, whose few entries put up to 256 slices on one
+// entry, use tsmttsm_cross_cta instead, with a tree over the slices.)
 // Every order above depends only on (G, M, N, tile), so results repeat bit
 // for bit.
 // Kernels with a tile chosen at launch pass its size (tm <= TM, tn <= TN;
@@ -156,6 +169,7 @@ template <int TM, int TN, int CC>
 __device__ __forceinline__ void tsmttsm_finish(const TsmttsmArgs& a, const double* acc, int PM, int PN,
                                                int L, int lane, int p, bool active, int tm = TM, int tn = TN) {
     __shared__ double red[kBlock * CC];
+    __shared__ unsigned s_last;
     const int M = a.M, N = a.N;
     const int P = PM * PN;
     const int t = threadIdx.x;
@@ -183,7 +197,55 @@ __device__ __forceinline__ void tsmttsm_finish(const TsmttsmArgs& a, const doubl
                 __syncthreads();
             }
 
-    tsmttsm_cross_cta<CC>(a, red);
+    if (a.final_pass) return;  // the partials are summed by the final kernel
+    __threadfence();
+    __syncthreads();
+    if (t == 0) s_last = (atomicAdd(a.ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int MN = M * N;
+    const int G = gridDim.x;
+    // S threads per entry when there are fewer entries than threads.
+    int S = 1;
+    while (S * 2 * MN <= (int)blockDim.x && S * 2 <= G) S *= 2;
+    for (int base = 0; base < MN * S; base += blockDim.x) {
+        const int w = base + t;
+        double v[CC];
+        const bool mine = w < MN * S;
+        if (mine) sum_partials<CC>(a.ws, MNc, w / S, G, w % S, S, v);
+        if (S > 1) {
+            // slice sums of one entry are adjacent threads: combine in order
+#pragma unroll
+            for (int c = 0; c < CC; ++c) red[t * CC + c] = mine ? v[c] : 0.0;
+            __syncthreads();
+            if (mine && (w % S) == 0)
+                for (int s = 1; s < S; ++s)
+#pragma unroll
+                    for (int c = 0; c < CC; ++c) v[c] += red[(t + s) * CC + c];
+            __syncthreads();
+        }
+        if (!mine || (w % S) != 0) continue;
+        const int o = w / S;
+        const int m = o / N, n = o - m * N;
+        double* out = a.C + ((int64_t)m * a.ldc + n) * CC;
+        if (CC == 1) {
+            double r = a.alpha_r * v[0];
+            if (!a.beta_zero) r = fma(a.beta_r, out[0], r);
+            out[0] = r;
+        } else {
+            double rr = a.alpha_r * v[0] - a.alpha_i * v[CC - 1];
+            double ri = a.alpha_r * v[CC - 1] + a.alpha_i * v[0];
+            if (!a.beta_zero) {
+                const double orr = out[0], oi = out[CC - 1];
+                rr += a.beta_r * orr - a.beta_i * oi;
+                ri += a.beta_r * oi + a.beta_i * orr;
+            }
+            out[0] = rr;
+            out[CC - 1] = ri;
+        }
+    }
+    if (t == 0) *a.ticket = 0u;
 }
 
 // TSMM output store: B[row][n] = acc (+ beta * B[row][n] unless beta == 0).
@@ -195,6 +257,25 @@ __device__ __forceinline__ void tsmm_store(const TsmmArgs& a, double* out, int n
     } else {
         if (!a.beta_zero) {
             const double orr = out[n * 2], oi = out[n * 2 + 1];
+            vr += a.beta_r * orr - a.beta_i * oi;
+            vi += a.beta_r * oi + a.beta_i * orr;
+        }
+        out[n * 2] = vr;
+        out[n * 2 + 1] = vi;
+    }
+}
+
+// As tsmm_store, with the old B[row][n] (or, ob) loaded earlier, together
+// with the row's A values, so that its latency overlaps the FMAs instead of
+// stalling the store (only read when beta != 0).
+template <int CC>
+__device__ __forceinline__ void tsmm_store_old(const TsmmArgs& a, double* out, int n, double vr, double vi,
+                                               double orr, double oi) {
+    if (CC == 1) {
+        if (!a.beta_zero) vr = fma(a.beta_r, orr, vr);
+        out[n] = vr;
+    } else {
+        if (!a.beta_zero) {
             vr += a.beta_r * orr - a.beta_i * oi;
             vi += a.beta_r * oi + a.beta_i * orr;
         }

@@ -56,13 +56,26 @@ __global__ void __launch_bounds__(kBlock) k_tsmm(const TsmmArgs a) {
             rok[u] = row[u] < a.K;
             if (!rok[u]) row[u] = 0;
         }
-        double acc[U][NPT][CC];
+        double acc[U][NPT][CC], ob[U][NPT][CC];
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
             for (int j = 0; j < NPT; ++j)
 #pragma unroll
-                for (int c = 0; c < CC; ++c) acc[u][j][c] = 0.0;
+                for (int c = 0; c < CC; ++c) acc[u][j][c] = ob[u][j][c] = 0.0;
+        if (!a.beta_zero) {
+            // old B values first, so their latency overlaps the FMAs
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int j = 0; j < NPT; ++j) {
+                    if (j >= npt) break;
+                    const int n = q + j * TPR;
+                    if (rok[u] && n < N)
+#pragma unroll
+                        for (int c = 0; c < CC; ++c) ob[u][j][c] = a.B[row[u] * sb + n * CC + c];
+                }
+        }
 #pragma unroll 2
         for (int m = 0; m < M; ++m) {
             double av[U][CC];
@@ -103,7 +116,7 @@ __global__ void __launch_bounds__(kBlock) k_tsmm(const TsmmArgs a) {
                 if (j >= npt) break;
                 const int n = q + j * TPR;
                 if (n >= N) continue;
-                tsmm_store<CC>(a, out, n, acc[u][j][0], acc[u][j][CC - 1]);
+                tsmm_store_old<CC>(a, out, n, acc[u][j][0], acc[u][j][CC - 1], ob[u][j][0], ob[u][j][CC - 1]);
             }
         }
     }
@@ -229,6 +242,48 @@ void register_fp64_variants(std::vector<Variant>& tsmttsm, std::vector<Variant>&
     add_tsmttsm<true>(tsmttsm);
     add_tsmm<false>(tsmm);
     add_tsmm<true>(tsmm);
+}
+
+namespace {
+
+// Final pass of the TSMTTSM reduction: S consecutive lanes of a warp share
+// entry o of C (S a power of two <= 32); lane s sums the CTA partials s,
+// s + S, ... in order (eight interleaved running sums, combined by a fixed
+// tree), the S slice sums are combined by a fixed shuffle tree, and the
+// first lane stores alpha * sum + beta * C.  With S chosen so that each
+// lane takes a few dozen partials, the pass is a handful of L2 round trips
+// however many CTAs wrote partials.
+template <int CC>
+__global__ void __launch_bounds__(256) k_tsmttsm_final(const TsmttsmArgs a, int G, int S) {
+    const int MN = a.M * a.N;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int o = gt / S, s = gt - o * S;  // S divides 32: an entry's lanes share a warp
+    double v[CC];
+    if (o < MN) {
+        sum_partials<CC>(a.ws, MN * CC, o, G, s, S, v);
+    } else {
+#pragma unroll
+        for (int c = 0; c < CC; ++c) v[c] = 0.0;
+    }
+    for (int h = S >> 1; h >= 1; h >>= 1)
+#pragma unroll
+        for (int c = 0; c < CC; ++c) v[c] += __shfl_down_sync(0xffffffffu, v[c], h, S);
+    if (o < MN && s == 0) tsmttsm_store_entry<CC>(a, o, v);
+}
+
+}  // namespace
+
+cudaError_t launch_tsmttsm_final(const TsmttsmArgs& a, int grid, int cplx, cudaStream_t s) {
+    const int MN = a.M * a.N;
+    int S = 1;
+    while (S < 32 && grid >= 16 * S) S *= 2;  // at least 8 partials per lane
+    const int threads = MN * S;
+    const int blocks = (threads + 255) / 256;
+    if (cplx)
+        k_tsmttsm_final<2><<<blocks, 256, 0, s>>>(a, grid, S);
+    else
+        k_tsmttsm_final<1><<<blocks, 256, 0, s>>>(a, grid, S);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_scale_small(double* C, int rows, int cols, int64_t ld, int cplx, double br, double bi,

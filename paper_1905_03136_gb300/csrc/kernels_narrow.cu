@@ -27,8 +27,11 @@
 //  - TSMM: alpha*C (at most 16 doubles) lives in registers (Sec. 4.2 "data
 //    from C": registers instead of shared memory) and each thread writes its
 //    group of R output rows with vector stores.
-// The loops are balanced: CTA b of G takes groups [NG*b/G, NG*(b+1)/G), so
-// every CTA streams the same number of bytes (+-1 group).
+// Two orders of the group loop.  Contiguous: CTA b of G takes groups
+// [NG*b/G, NG*(b+1)/G), every CTA streaming the same bytes (+-1 group).
+// Window: chunks of U blocks of 256 groups, CTA b taking chunks b, b + G,
+// ..., so the grid moves through the arrays together (better DRAM page
+// locality when reads and writes mix, as in TSMM, which always uses it).
 #include <cstdio>
 #include <cstring>
 
@@ -114,7 +117,7 @@ __device__ __forceinline__ void row_fma(const double* a, const double* b, double
 
 // --------------------------------------------------------------- TSMTTSM
 
-template <int M, int N, int CC, bool CONJ, int VW, int U, bool PF>
+template <int M, int N, int CC, bool CONJ, int VW, int U, bool PF, bool WIN>
 __global__ void __launch_bounds__(kBlock) k_tsmttsm_narrow(const TsmttsmArgs a, int vec) {
     typedef Group<M, N, CC, VW> Gp;
     constexpr int R = Gp::R, EA = Gp::EA, EB = Gp::EB, MNC = M * N * CC;
@@ -125,7 +128,91 @@ __global__ void __launch_bounds__(kBlock) k_tsmttsm_narrow(const TsmttsmArgs a, 
     const int t = threadIdx.x;
     const int64_t G = gridDim.x, b = blockIdx.x;
 
-    if (vec) {
+    if (vec && WIN) {
+        // Window order: the NB whole blocks of 256 groups are cut into
+        // G * T chunks of at most U blocks; CTA b takes chunks b, b + G,
+        // ..., so at any moment the grid streams one window of consecutive
+        // chunks (DRAM pages shared by neighbouring CTAs).  A chunk's block
+        // count is CTA-uniform, so no warp diverges.
+        const int64_t NG = a.K / R, NB = NG / kBlock;
+        const int64_t T = (NB + G * U - 1) / (G * U), NC = G * T;
+        auto load = [&](int64_t c, double (*av)[EA], double (*bv)[EB]) -> int {
+            const int64_t blk0 = NB * c / NC;
+            const int nb = (int)(NB * (c + 1) / NC - blk0);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (u >= nb) break;
+                const int64_t g = (blk0 + u) * kBlock + t;
+#pragma unroll
+                for (int v = 0; v < EA / VW; ++v) ldv<VW>(a.A + g * EA + v * VW, &av[u][v * VW]);
+#pragma unroll
+                for (int v = 0; v < EB / VW; ++v) ldv<VW>(a.B + g * EB + v * VW, &bv[u][v * VW]);
+            }
+            return nb;
+        };
+        auto compute = [&](int nb, double (*av)[EA], double (*bv)[EB]) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (u >= nb) break;
+#pragma unroll
+                for (int r = 0; r < R; ++r) row_fma<M, N, CC, CONJ>(&av[u][r * M * CC], &bv[u][r * N * CC], acc);
+            }
+        };
+        if (PF) {
+            int64_t c = b;
+            if (c < NC) {
+                double av[U][EA], bv[U][EB];
+                int nb = load(c, av, bv);
+                for (;;) {
+                    const int64_t cn = c + G;
+                    if (cn < NC) {
+                        double an[U][EA], bn[U][EB];
+                        const int nn = load(cn, an, bn);
+                        compute(nb, av, bv);
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+#pragma unroll
+                            for (int e = 0; e < EA; ++e) av[u][e] = an[u][e];
+#pragma unroll
+                            for (int e = 0; e < EB; ++e) bv[u][e] = bn[u][e];
+                        }
+                        nb = nn;
+                        c = cn;
+                    } else {
+                        compute(nb, av, bv);
+                        break;
+                    }
+                }
+            }
+        } else {
+            for (int64_t c = b; c < NC; c += G) {
+                double av[U][EA], bv[U][EB];
+                const int nb = load(c, av, bv);
+                compute(nb, av, bv);
+            }
+        }
+        // the groups after the last whole block and the rows after the last
+        // whole group
+        if (b == G - 1) {
+            for (int64_t g = NB * kBlock + t; g < NG; g += kBlock) {
+                double av[EA], bv[EB];
+#pragma unroll
+                for (int v = 0; v < EA / VW; ++v) ldv<VW>(a.A + g * EA + v * VW, &av[v * VW]);
+#pragma unroll
+                for (int v = 0; v < EB / VW; ++v) ldv<VW>(a.B + g * EB + v * VW, &bv[v * VW]);
+#pragma unroll
+                for (int r = 0; r < R; ++r) row_fma<M, N, CC, CONJ>(&av[r * M * CC], &bv[r * N * CC], acc);
+            }
+            for (int64_t k = NG * R + t; k < a.K; k += kBlock) {
+                double av[M * CC], bv[N * CC];
+#pragma unroll
+                for (int e = 0; e < M * CC; ++e) av[e] = __ldg(a.A + k * (M * CC) + e);
+#pragma unroll
+                for (int e = 0; e < N * CC; ++e) bv[e] = __ldg(a.B + k * (N * CC) + e);
+                row_fma<M, N, CC, CONJ>(av, bv, acc);
+            }
+        }
+    } else if (vec) {
         const int64_t NG = a.K / R;
         const int64_t g1 = NG * (b + 1) / G;
         int64_t g = NG * b / G + t;
@@ -239,22 +326,22 @@ bool narrow_vec_ok(const double* A, int64_t lda, const double* B, int64_t ldb) {
     return lda == M && ldb == N && ((uintptr_t)A % (VW * 8)) == 0 && ((uintptr_t)B % (VW * 8)) == 0;
 }
 
-template <int M, int N, int CC, int VW, int U, bool PF>
+template <int M, int N, int CC, int VW, int U, bool PF, bool WIN>
 cudaError_t launch_tsmttsm_narrow(const TsmttsmArgs& a, int grid, cudaStream_t s) {
     if (a.M != M || a.N != N) return cudaErrorInvalidValue;
     const int vec = narrow_vec_ok<M, N, CC, VW>(a.A, a.lda, a.B, a.ldb) ? 1 : 0;
     if (CC == 2 && a.conj)
-        k_tsmttsm_narrow<M, N, CC, true, VW, U, PF><<<grid, kBlock, 0, s>>>(a, vec);
+        k_tsmttsm_narrow<M, N, CC, true, VW, U, PF, WIN><<<grid, kBlock, 0, s>>>(a, vec);
     else
-        k_tsmttsm_narrow<M, N, CC, false, VW, U, PF><<<grid, kBlock, 0, s>>>(a, vec);
+        k_tsmttsm_narrow<M, N, CC, false, VW, U, PF, WIN><<<grid, kBlock, 0, s>>>(a, vec);
     return cudaGetLastError();
 }
 
-template <int M, int N, int CC, int VW, int U, bool PF>
+template <int M, int N, int CC, int VW, int U, bool PF, bool WIN>
 int occ_tsmttsm_narrow(int, int) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tsmttsm_narrow<M, N, CC, false, VW, U, PF>, kBlock,
-                                                      0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tsmttsm_narrow<M, N, CC, false, VW, U, PF, WIN>,
+                                                      kBlock, 0) != cudaSuccess)
         return 0;
     return n;
 }
@@ -318,49 +405,62 @@ __global__ void __launch_bounds__(kBlock) k_tsmm_narrow(const TsmmArgs a, int ve
     };
 
     if (vec) {
-        const int64_t NG = a.K / R;
-        const int64_t g1 = NG * (b + 1) / G;
-        int64_t g = NG * b / G + t;
-        auto load = [&](int64_t g0, double (*av)[EA], double (*bo)[EB]) {
+        // Window order (as in the TSMTTSM kernel): G * T chunks of at most U
+        // blocks of 256 groups, CTA b taking chunks b, b + G, ...; reads and
+        // writes of the whole grid then move through one window of the
+        // arrays, which keeps DRAM pages open for both directions (separate
+        // per-CTA ranges interleave 2 G streams in the banks).
+        const int64_t NG = a.K / R, NB = NG / kBlock;
+        const int64_t T = (NB + G * U - 1) / (G * U), NC = G * T;
+        auto load = [&](int64_t c, double (*av)[EA], double (*bo)[EB], int64_t* blk) -> int {
+            const int64_t blk0 = NB * c / NC;
+            const int nb = (int)(NB * (c + 1) / NC - blk0);
+            *blk = blk0;
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const double* pa = a.A + (g0 + (int64_t)u * kBlock) * EA;
+                if (u >= nb) break;
+                const int64_t g = (blk0 + u) * kBlock + t;
 #pragma unroll
-                for (int v = 0; v < EA / VW; ++v) ldv<VW>(pa + v * VW, &av[u][v * VW]);
+                for (int v = 0; v < EA / VW; ++v) ldv<VW>(a.A + g * EA + v * VW, &av[u][v * VW]);
             }
             if (!bz) {
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    const double* pb = a.B + (g0 + (int64_t)u * kBlock) * EB;
+                    if (u >= nb) break;
+                    const int64_t g = (blk0 + u) * kBlock + t;
 #pragma unroll
-                    for (int v = 0; v < EB / VW; ++v) ldv_rw<VW>(pb + v * VW, &bo[u][v * VW]);
+                    for (int v = 0; v < EB / VW; ++v) ldv_rw<VW>(a.B + g * EB + v * VW, &bo[u][v * VW]);
                 }
             }
+            return nb;
         };
-        auto compute_store = [&](int64_t g0, double (*av)[EA], double (*bo)[EB]) {
+        auto compute_store = [&](int64_t blk0, int nb, double (*av)[EA], double (*bo)[EB]) {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
+                if (u >= nb) break;
                 double out[EB];
 #pragma unroll
                 for (int r = 0; r < R; ++r) row_out(&av[u][r * M * CC], &bo[u][r * N * CC], &out[r * N * CC]);
-                double* pb = a.B + (g0 + (int64_t)u * kBlock) * EB;
+                double* pb = a.B + ((blk0 + u) * kBlock + t) * EB;
 #pragma unroll
                 for (int v = 0; v < EB / VW; ++v) stv<VW>(pb + v * VW, &out[v * VW]);
             }
         };
-        const int64_t step = (int64_t)U * kBlock;
         if (PF) {
-            // the loads of the next U groups are in flight while the
-            // current ones are computed and stored (register double buffer)
-            if (g + (int64_t)(U - 1) * kBlock < g1) {
+            // the next chunk's loads are in flight while the current chunk
+            // is computed and stored (register double buffer)
+            int64_t c = b;
+            if (c < NC) {
                 double av[U][EA], bo[U][EB];
-                load(g, av, bo);
+                int64_t blk;
+                int nb = load(c, av, bo, &blk);
                 for (;;) {
-                    const int64_t gn = g + step;
-                    if (gn + (int64_t)(U - 1) * kBlock < g1) {
+                    const int64_t cn = c + G;
+                    if (cn < NC) {
                         double an[U][EA], bn[U][EB];
-                        load(gn, an, bn);
-                        compute_store(g, av, bo);
+                        int64_t blkn;
+                        const int nn = load(cn, an, bn, &blkn);
+                        compute_store(blk, nb, av, bo);
 #pragma unroll
                         for (int u = 0; u < U; ++u) {
 #pragma unroll
@@ -368,35 +468,38 @@ __global__ void __launch_bounds__(kBlock) k_tsmm_narrow(const TsmmArgs a, int ve
 #pragma unroll
                             for (int e = 0; e < EB; ++e) bo[u][e] = bn[u][e];
                         }
-                        g = gn;
+                        nb = nn;
+                        blk = blkn;
+                        c = cn;
                     } else {
-                        compute_store(g, av, bo);
-                        g = gn;
+                        compute_store(blk, nb, av, bo);
                         break;
                     }
                 }
             }
         } else {
-            for (; g + (int64_t)(U - 1) * kBlock < g1; g += step) {
+            for (int64_t c = b; c < NC; c += G) {
                 double av[U][EA], bo[U][EB];
-                load(g, av, bo);
-                compute_store(g, av, bo);
+                int64_t blk;
+                const int nb = load(c, av, bo, &blk);
+                compute_store(blk, nb, av, bo);
             }
         }
-        for (; g < g1; g += kBlock) {
-            double av[EA], bo[EB], out[EB];
-#pragma unroll
-            for (int v = 0; v < EA / VW; ++v) ldv<VW>(a.A + g * EA + v * VW, &av[v * VW]);
-            if (!bz) {
-#pragma unroll
-                for (int v = 0; v < EB / VW; ++v) ldv_rw<VW>(a.B + g * EB + v * VW, &bo[v * VW]);
-            }
-#pragma unroll
-            for (int r = 0; r < R; ++r) row_out(&av[r * M * CC], &bo[r * N * CC], &out[r * N * CC]);
-#pragma unroll
-            for (int v = 0; v < EB / VW; ++v) stv<VW>(a.B + g * EB + v * VW, &out[v * VW]);
-        }
+        // groups after the last whole block, rows after the last whole group
         if (b == G - 1) {
+            for (int64_t g = NB * kBlock + t; g < NG; g += kBlock) {
+                double av[EA], bo[EB], out[EB];
+#pragma unroll
+                for (int v = 0; v < EA / VW; ++v) ldv<VW>(a.A + g * EA + v * VW, &av[v * VW]);
+                if (!bz) {
+#pragma unroll
+                    for (int v = 0; v < EB / VW; ++v) ldv_rw<VW>(a.B + g * EB + v * VW, &bo[v * VW]);
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r) row_out(&av[r * M * CC], &bo[r * N * CC], &out[r * N * CC]);
+#pragma unroll
+                for (int v = 0; v < EB / VW; ++v) stv<VW>(a.B + g * EB + v * VW, &out[v * VW]);
+            }
             for (int64_t k = NG * R + t; k < a.K; k += kBlock) {
                 double av[M * CC], bo[N * CC], out[N * CC];
 #pragma unroll
@@ -447,12 +550,12 @@ int occ_tsmm_narrow(int, int) {
 
 // ----------------------------------------------------------- registration
 
-template <int M, int N, int CC, int VW, int U, bool PF>
+template <int M, int N, int CC, int VW, int U, bool PF, bool WIN>
 Variant make_tsmttsm_narrow() {
     Variant v;
     memset(&v, 0, sizeof(v));
-    snprintf(v.info.name, sizeof(v.info.name), "tsmttsm_%s_narrow_m%dn%d_v%d_u%d%s", CC == 2 ? "c64" : "r64", M,
-             N, VW, U, PF ? "_pf" : "");
+    snprintf(v.info.name, sizeof(v.info.name), "tsmttsm_%s_narrow_m%dn%d_v%d_u%d%s%s", CC == 2 ? "c64" : "r64",
+             M, N, VW, U, PF ? "_pf" : "", WIN ? "_win" : "");
     v.info.kind = TSM_KIND_TSMTTSM;
     v.info.dtype = CC == 2 ? TSM_C64 : TSM_R64;
     v.info.fixed_m = M;
@@ -461,8 +564,8 @@ Variant make_tsmttsm_narrow() {
     v.info.tile_n = N;
     v.info.unroll = U;
     v.info.block = kBlock;
-    v.tsmttsm = launch_tsmttsm_narrow<M, N, CC, VW, U, PF>;
-    v.occupancy = occ_tsmttsm_narrow<M, N, CC, VW, U, PF>;
+    v.tsmttsm = launch_tsmttsm_narrow<M, N, CC, VW, U, PF, WIN>;
+    v.occupancy = occ_tsmttsm_narrow<M, N, CC, VW, U, PF, WIN>;
     return v;
 }
 
@@ -487,16 +590,19 @@ Variant make_tsmm_narrow() {
 
 // Variants per product and shape: 16-byte vectors with four groups in
 // flight, 32-byte vectors with two and with four, and vectors with the next
-// groups prefetched into a second register buffer ("_pf").  TSMM
+// groups prefetched into a second register buffer ("_pf"); TSMTTSM also in
+// window order ("_win"; TSMM always streams in window order).  TSMM
 // holds its output group beside the loaded one, so wide groups (real 3 x 3:
 // 12 doubles each) take a smaller unroll (MU) to stay clear of spills.
 template <int M, int N, int CC, int MU>
 void add_shape(std::vector<Variant>& t, std::vector<Variant>& m) {
-    t.push_back(make_tsmttsm_narrow<M, N, CC, 2, 4, false>());
-    t.push_back(make_tsmttsm_narrow<M, N, CC, 4, 2, false>());
-    t.push_back(make_tsmttsm_narrow<M, N, CC, 4, 4, false>());
-    t.push_back(make_tsmttsm_narrow<M, N, CC, 4, 1, true>());
-    t.push_back(make_tsmttsm_narrow<M, N, CC, 4, 2, true>());
+    t.push_back(make_tsmttsm_narrow<M, N, CC, 2, 4, false, false>());
+    t.push_back(make_tsmttsm_narrow<M, N, CC, 4, 2, false, false>());
+    t.push_back(make_tsmttsm_narrow<M, N, CC, 4, 4, false, false>());
+    t.push_back(make_tsmttsm_narrow<M, N, CC, 4, 1, true, false>());
+    t.push_back(make_tsmttsm_narrow<M, N, CC, 4, 2, true, false>());
+    t.push_back(make_tsmttsm_narrow<M, N, CC, 4, 1, true, true>());
+    t.push_back(make_tsmttsm_narrow<M, N, CC, 4, 2, true, true>());
     m.push_back(make_tsmm_narrow<M, N, CC, 2, MU, false>());
     m.push_back(make_tsmm_narrow<M, N, CC, 4, (MU > 2 ? MU / 2 : 1), false>());
     m.push_back(make_tsmm_narrow<M, N, CC, 4, MU, false>());

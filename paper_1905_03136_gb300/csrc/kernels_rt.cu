@@ -70,13 +70,26 @@ __global__ void __launch_bounds__(kBlock) k_tsmm_rt(const TsmmArgs a, const int 
             rok[u] = live && row[u] < a.K;
             if (!rok[u]) row[u] = 0;
         }
-        double acc[U][NPT][CC];
+        double acc[U][NPT][CC], ob[U][NPT][CC];
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
             for (int j = 0; j < NPT; ++j)
 #pragma unroll
-                for (int c = 0; c < CC; ++c) acc[u][j][c] = 0.0;
+                for (int c = 0; c < CC; ++c) acc[u][j][c] = ob[u][j][c] = 0.0;
+        if (!a.beta_zero) {
+            // old B values first, so their latency overlaps the FMAs
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int j = 0; j < NPT; ++j) {
+                    if (j >= npt) break;
+                    const int n = q + j * tpr;
+                    if (rok[u] && n < N)
+#pragma unroll
+                        for (int c = 0; c < CC; ++c) ob[u][j][c] = a.B[row[u] * sb + n * CC + c];
+                }
+        }
         if (live) {
 #pragma unroll 2
             for (int m = 0; m < M; ++m) {
@@ -117,7 +130,7 @@ __global__ void __launch_bounds__(kBlock) k_tsmm_rt(const TsmmArgs a, const int 
                 if (j >= npt) break;
                 const int n = q + j * tpr;
                 if (n >= N) continue;
-                tsmm_store<CC>(a, out, n, acc[u][j][0], acc[u][j][CC - 1]);
+                tsmm_store_old<CC>(a, out, n, acc[u][j][0], acc[u][j][CC - 1], ob[u][j][0], ob[u][j][CC - 1]);
             }
         }
     }

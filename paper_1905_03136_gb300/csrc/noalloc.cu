@@ -103,5 +103,6 @@ extern "C" tsm_status tsm_tsmttsm_noalloc(tsm_op opA, tsm_dtype dtype, int M, in
     a.conj = (cplx && opA == TSM_OP_C) ? 1 : 0;
     a.ws = static_cast<double*>(scratch);
     a.ticket = ticket;
+    a.final_pass = 0;  // the last CTA sums the partials: no second launch
     return var->tsmttsm(a, grid, s) == cudaSuccess ? TSM_OK : TSM_ERR_LAUNCH;
 }

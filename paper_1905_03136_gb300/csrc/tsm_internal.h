@@ -27,6 +27,8 @@ struct TsmttsmArgs {
     int conj;         // 1: A^H B
     double* ws;       // grid * M * N * c partial sums
     unsigned* ticket; // one counter, zero between launches
+    int final_pass;   // 1: CTAs only write their partials; a separate final
+                      // kernel (launch_tsmttsm_final) sums them afterwards
 };
 
 // Arguments of one TSMM launch.
@@ -61,6 +63,14 @@ void register_fp64_variants(std::vector<Variant>& tsmttsm, std::vector<Variant>&
 void register_generated_variants(std::vector<Variant>& tsmttsm, std::vector<Variant>& tsmm);
 void register_rt_variants(std::vector<Variant>& tsmttsm, std::vector<Variant>& tsmm);
 void register_narrow_variants(std::vector<Variant>& tsmttsm, std::vector<Variant>& tsmm);
+
+// Second pass of the TSMTTSM reduction when the partials are many
+// (grid * M * N * c > kFinalThreshold doubles): one thread per entry of C
+// sums the `grid` CTA partials in CTA order and applies alpha/beta.  Spread
+// over ceil(M*N / 128) CTAs, this replaces the last CTA's single-SM sum,
+// whose FP64 adds alone would take grid * M*N*c / 2 cycles on this part.
+constexpr int kFinalThreshold = 32768;
+cudaError_t launch_tsmttsm_final(const TsmttsmArgs& a, int grid, int cplx, cudaStream_t s);
 
 // Per-launch choice of the runtime-threads-per-row TSMM variants (kernels_rt.cu).
 void rt_tsmm_tpr(int N, int nptmax, int* tpr, int* npt);

@@ -145,6 +145,16 @@ tsm_status tsm_set_tuning(tsm_kind kind, tsm_dtype dtype, int M, int N, int64_t 
     return TSM_OK;
 }
 
+tsm_status tsm_set_tuning_timed(tsm_kind kind, tsm_dtype dtype, int M, int N, int64_t K, int variant, int grid,
+                                float ms) {
+    const Variant* v = variant_at(kind, variant);
+    if (!v || !supports(kind, variant, dtype, M, N) || grid < 0) return TSM_ERR_INVALID_VALUE;
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_env_loaded = true;
+    g_table[Key(kind, dtype, M, N, k_bucket(K))] = Entry{v->info.name, grid, ms};
+    return TSM_OK;
+}
+
 tsm_status tsm_tune_grids(tsm_kind kind, int variant, tsm_dtype dtype, int M, int N, int* grids, int max,
                           int* count) {
     if (!grids || !count || max < 0) return TSM_ERR_INVALID_VALUE;

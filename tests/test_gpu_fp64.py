@@ -199,7 +199,7 @@ NARROW = [(False, 1, 1), (False, 2, 2), (False, 3, 3), (False, 4, 4), (True, 1, 
 def _narrow(tsm, kind, cplx, M, N):
     pre = "%s_%s_narrow_m%dn%d_" % ("tsmttsm" if kind == tsm.KIND_TSMTTSM else "tsmm", "c64" if cplx else "r64", M, N)
     vs = [v["index"] for v in tsm.variants(kind) if v["name"].startswith(pre)]
-    assert len(vs) == 5, pre
+    assert len(vs) == (7 if kind == tsm.KIND_TSMTTSM else 5), pre
     return vs
 
 
@@ -272,6 +272,44 @@ def test_narrow_variants_every_layout(tsm, case):
                 tsm.tsmm(a, dC, out, alpha, beta, variant=v)
                 err = oracle.rel_fro(host(out), ref1)
                 assert err <= TOL, (tsm.variants(tsm.KIND_TSMM)[v]["name"], K, lay, "beta", err)
+
+
+@pytest.mark.parametrize("cplx", [False, True], ids=["r64", "c64"])
+def test_every_width_fixed_shape_kernels(tsm, cplx):
+    """Every width-specialised kernel (the code generator's and the narrow
+    family's) for every square width 1..64: TSMTTSM and TSMM (beta = 0 and
+    beta != 0) against the oracle on a ragged row count."""
+    K = 1031
+    dt = tsm.C64 if cplx else tsm.R64
+    alpha, beta = (0.5 + 0.25j, -1.0 + 0.5j) if cplx else (0.5, -1.0)
+    tv = tsm.variants(tsm.KIND_TSMTTSM)
+    mv = tsm.variants(tsm.KIND_TSMM)
+    seen = 0
+    for w in range(1, 65):
+        A = synth.block_vector(71, K, w, complex_=cplx)
+        B = synth.block_vector(72, K, w, complex_=cplx)
+        Cm = synth.small_matrix(73, w, w, complex_=cplx)
+        dA, dB, dC = dev(A), dev(B), dev(Cm)
+        ref_t = oracle.gram(A, B, "C" if cplx else "T")
+        fixed_t = [v for v in _variants_for(tsm, tsm.KIND_TSMTTSM, dt, w, w) if tv[v]["fixed_m"] == w]
+        fixed_m = [v for v in _variants_for(tsm, tsm.KIND_TSMM, dt, w, w) if mv[v]["fixed_m"] == w]
+        # every width has a TSMM kernel of its own; so has every TSMTTSM width
+        # except complex 64, whose 64 x 64 x 2 accumulators are served by the
+        # hand-written 8 x 4 tiles (tested above)
+        assert fixed_m and (fixed_t or (cplx and w == 64)), ("no width-specialised kernel", w)
+        for v in fixed_t:
+            C = host(tsm.tsmttsm(dA, dB, op="C" if cplx else "T", variant=v))
+            assert oracle.rel_fro(C, ref_t) <= TOL, (tv[v]["name"], w)
+            seen += 1
+        ref0 = oracle.apply(A, Cm)
+        ref1 = oracle.apply(A, Cm, alpha, beta, B)
+        for v in fixed_m:
+            assert oracle.rel_fro(host(tsm.tsmm(dA, dC, variant=v)), ref0) <= TOL, (mv[v]["name"], w)
+            out = dev(B)
+            tsm.tsmm(dA, dC, out, alpha, beta, variant=v)
+            assert oracle.rel_fro(host(out), ref1) <= TOL, (mv[v]["name"], w, "beta")
+            seen += 1
+    assert seen >= 127
 
 
 def test_device_fill_matches_host_generator(tsm):
