@@ -87,9 +87,11 @@ tsm_status tsm_tsmttsm(tsm_op opA, tsm_dtype dtype, int M, int N, int64_t K,
 
 /*
  * TSMM (Sec. 4): B = alpha * A C + beta * B in binary64.  A: K x M (lda >= M),
- * C: M x N (ldc >= N), B: K x N (ldb >= N).  C is staged once per CTA in
- * shared memory (Sec. 4.2); rows of B are independent, so there is no
- * reduction.  opC must be TSM_OP_N.  Errors as for tsm_tsmttsm.
+ * C: M x N (ldc >= N), B: K x N (ldb >= N).  alpha * C is staged once per
+ * CTA in shared memory or registers (Sec. 4.2); rows of B are independent,
+ * so there is no reduction.  With beta != 0 each old B value is read with
+ * the row's A values and starts its FMA chain (as it is for beta == 1).
+ * opC must be TSM_OP_N.  Errors as for tsm_tsmttsm.
  */
 tsm_status tsm_tsmm(tsm_op opC, tsm_dtype dtype, int M, int N, int64_t K,
                     const double *alpha, const void *A, int64_t lda,
@@ -116,7 +118,16 @@ tsm_status tsm_release(void);
  * specialisation to fixed M, N by the code generator (Sec. 2.1).  The
  * autotuner and tests address them by index.
  */
-typedef enum { TSM_KIND_TSMTTSM = 0, TSM_KIND_TSMM = 1 } tsm_kind;
+typedef enum {
+    TSM_KIND_TSMTTSM = 0,
+    TSM_KIND_TSMM = 1,
+    /* TSMM with beta != 0, which also streams B in: a tuning-table key of
+     * its own (the best kernel for three streams differs from the best for
+     * two).  It names the same variants as TSM_KIND_TSMM; tsm_tune and
+     * tsm_time_variant time them with beta = 1, and a TSMM call with
+     * beta != 0 looks this key up first, then the TSM_KIND_TSMM entry. */
+    TSM_KIND_TSMM_BETA = 2
+} tsm_kind;
 
 typedef struct {
     char name[64];  /* e.g. "tsmttsm_r64_direct_t4x4_u2" */
@@ -151,6 +162,12 @@ tsm_status tsm_variant_shape(tsm_kind kind, int index, tsm_dtype dtype, int M, i
 
 /* 1 if variant `index` can run (op, dtype, M, N), else 0. */
 int tsm_variant_supports(tsm_kind kind, int index, tsm_dtype dtype, int M, int N);
+
+/* Kernel launches one TSMTTSM call of shape (dtype, M, N) makes with `grid`
+ * CTAs: 1, or 2 when the CTA partials (grid * M * N doubles, twice that for
+ * complex) are many enough that a separate final kernel sums them (Sec. 3.2
+ * reduction, second pass).  -1 for a shape outside [1, 64] or grid < 1. */
+int tsm_tsmttsm_kernels_per_call(tsm_dtype dtype, int M, int N, int grid);
 
 /*
  * As tsm_tsmttsm / tsm_tsmm but with an explicit variant and grid size

@@ -36,7 +36,10 @@ typedef struct {
  * `reps` calls each after one warm-up call, records the fastest in the
  * tuning table under (kind, dtype, M, N, floor(log2 K)), and writes up to
  * max_samples measurements to `samples` (may be NULL; *n_samples gets the
- * total count).  NOT_SUPPORTED if no variant fits.
+ * total count).  NOT_SUPPORTED if no variant fits.  X, Y, Z are the
+ * operands in the order of the product's call: TSMTTSM A, B, C; TSMM A, C,
+ * B.  With kind TSM_KIND_TSMM_BETA the TSMM variants run with beta = 1, so
+ * Z (B) is read as well and must hold finite values.
  */
 tsm_status tsm_tune(tsm_kind kind, tsm_dtype dtype, int M, int N, int64_t K,
                     const void *X, int64_t ldx, const void *Y, int64_t ldy,
@@ -44,7 +47,8 @@ tsm_status tsm_tune(tsm_kind kind, tsm_dtype dtype, int M, int N, int64_t K,
                     int max_samples, int *n_samples, tsm_stream_t stream);
 
 /* Mean milliseconds of `reps` calls of one variant at one grid size (grid
- * <= 0: the variant's default).  NOT_SUPPORTED if it cannot run the shape. */
+ * <= 0: the variant's default), with beta = 1 for TSM_KIND_TSMM_BETA.
+ * NOT_SUPPORTED if it cannot run the shape. */
 tsm_status tsm_time_variant(tsm_kind kind, tsm_dtype dtype, int M, int N,
                             int64_t K, const void *X, int64_t ldx,
                             const void *Y, int64_t ldy, void *Z, int64_t ldz,

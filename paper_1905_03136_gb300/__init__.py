@@ -12,7 +12,7 @@ stride(0)) of float64 or complex128 device memory.
 import ctypes
 
 from . import _lib
-from ._lib import (C64, KIND_TSMM, KIND_TSMTTSM, OP_C, OP_N, OP_T, R64, TsmError, VariantInfo,
+from ._lib import (C64, KIND_TSMM, KIND_TSMM_BETA, KIND_TSMTTSM, OP_C, OP_N, OP_T, R64, TsmError, VariantInfo,
                    TuneSample, call, load, raw, scalar)
 
 __all__ = ["tsmttsm", "tsmm", "gs_step", "fill_random", "variants", "variant_shape", "choose", "tune", "time_variant",
@@ -152,7 +152,8 @@ def choose(kind, dtype, M, N, K):
 
 
 def tune(kind, X, Y, Z, reps=3, stream=None, max_samples=512):
-    """Exhaustive search (tsm_tune) on device tensors; returns the samples."""
+    """Exhaustive search (tsm_tune) on device tensors; returns the samples.
+    kind KIND_TSMM_BETA times the TSMM variants with beta = 1 (Z is read)."""
     dt = _dtype_code(X)
     if kind == KIND_TSMTTSM:
         K, M = X.shape

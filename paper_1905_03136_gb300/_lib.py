@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "TSM_OK", 1: "TSM_ERR_INVALID_VALUE", 2: "TSM_ERR_NOT_SUPPORT
                 4: "TSM_ERR_LAUNCH", 5: "TSM_ERR_TIMEOUT", 6: "TSM_ERR_INTERNAL", 7: "TSM_ERR_NO_DEVICE"}
 R64, C64 = 0, 1
 OP_N, OP_T, OP_C = 0, 1, 2
-KIND_TSMTTSM, KIND_TSMM = 0, 1
+KIND_TSMTTSM, KIND_TSMM, KIND_TSMM_BETA = 0, 1, 2
 
 
 class TsmError(RuntimeError):
@@ -59,6 +59,7 @@ SIGNATURES = {
     "tsm_variant_count": (i32, [i32]),
     "tsm_variant_get": (i32, [i32, i32, ctypes.POINTER(VariantInfo)]),
     "tsm_variant_supports": (i32, [i32, i32, i32, i32, i32]),
+    "tsm_tsmttsm_kernels_per_call": (i32, [i32, i32, i32, i32]),
     "tsm_choose": (i32, [i32, i32, i32, i32, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
     "tsm_fill_random": (i32, [vp, i32, i64, i64, i64, u64, i32, vp]),
     "tsm_tune": (i32, [i32, i32, i32, i32, i64, vp, i64, vp, i64, vp, i64, i32,

@@ -43,7 +43,8 @@ def _operands(kind, cplx, M, N, K, flatA, flatB):
         Z = torch.zeros(M * N * c, dtype=torch.float64, device=flatA.device)
     else:
         Y = flatB[: M * N * c]
-        Z = torch.empty(K * N * c, dtype=torch.float64, device=flatA.device)
+        # kind 2 (TSMM with beta = 1) reads B: finite values
+        Z = (torch.zeros if kind == 2 else torch.empty)(K * N * c, dtype=torch.float64, device=flatA.device)
     if cplx:
         X, Y, Z = (t.view(torch.complex128) for t in (X, Y, Z))
     X = X.view(K, M)
@@ -95,7 +96,7 @@ def tune_pruned(kind, shapes, K, model, topk=5, reps=1, log=None, flat=None, wit
         ms, v, g, p = min(timed, key=lambda x: x[0])
         _lib.call("tsm_set_tuning_timed", kind, int(cplx), M, N, K, v["index"], g, ms)
         print("%s %s %dx%d pruned best %s grid=%d %.4f ms (model %.4f; %d of %d timed, %.1fs)" % (
-            "tsmttsm" if kind == 0 else "tsmm", "c64" if cplx else "r64", M, N, v["name"], g, ms, p,
+            ("tsmttsm", "tsmm", "tsmm_beta")[kind], "c64" if cplx else "r64", M, N, v["name"], g, ms, p,
             len(timed), len(cands), time.time() - t0), flush=True)
         del X, Y, Z
     return records
@@ -116,19 +117,7 @@ def tune_shapes(kind, shapes, K, reps=3, log=None, flat=None):
         flatA, flatB = flat
     records = []
     for (cplx, M, N) in shapes:
-        c = 2 if cplx else 1
-        X = flatA[: K * M * c]
-        if kind == 0:
-            Y = flatB[: K * N * c]
-            Z = torch.zeros(M * N * c, dtype=torch.float64, device="cuda")
-        else:
-            Y = flatB[: M * N * c]
-            Z = torch.empty(K * N * c, dtype=torch.float64, device="cuda")
-        if cplx:
-            X, Y, Z = (t.view(torch.complex128) for t in (X, Y, Z))
-        X = X.view(K, M)
-        Y = Y.view(K, N) if kind == 0 else Y.view(M, N)
-        Z = Z.view(M, N) if kind == 0 else Z.view(K, N)
+        X, Y, Z = _operands(kind, cplx, M, N, K, flatA, flatB)
         t0 = time.time()
         samples = tsm.tune(kind, X, Y, Z, reps=reps)
         for (v, g, ms) in samples:
@@ -144,7 +133,7 @@ def tune_shapes(kind, shapes, K, reps=3, log=None, flat=None):
             log.flush()
         best = min(samples, key=lambda s: s[2])
         print("%s %s %dx%d best %s grid=%d %.4f ms (%d samples, %.1fs)" % (
-            "tsmttsm" if kind == 0 else "tsmm", "c64" if cplx else "r64", M, N, info[best[0]]["name"],
+            ("tsmttsm", "tsmm", "tsmm_beta")[kind], "c64" if cplx else "r64", M, N, info[best[0]]["name"],
             best[1], best[2], len(samples), time.time() - t0), flush=True)
         del X, Y, Z
     return records
@@ -174,7 +163,8 @@ def _has_entry(kind, shape, K):
 def main():
     ap = argparse.ArgumentParser(description="exhaustive autotuning of libtsm variants")
     ap.add_argument("--K", type=int, default=1 << 24)
-    ap.add_argument("--kind", choices=("tsmttsm", "tsmm", "both"), default="both")
+    ap.add_argument("--kind", choices=("tsmttsm", "tsmm", "tsmm_beta", "both"), default="both",
+                    help="tsmm_beta: TSMM timed with beta = 1, kept under its own table key")
     ap.add_argument("--table", default=DEFAULT_TABLE)
     ap.add_argument("--log", default=None, help="append measurements (JSON lines) here")
     ap.add_argument("--reps", type=int, default=3)
@@ -205,7 +195,7 @@ def main():
     flatB = torch.empty(K * 128, dtype=torch.float64, device="cuda")
     tsm.fill_random(flatA.view(K, 128), 0)
     tsm.fill_random(flatB.view(K, 128), 1)
-    kinds = {"tsmttsm": [0], "tsmm": [1], "both": [0, 1]}[args.kind]
+    kinds = {"tsmttsm": [0], "tsmm": [1], "tsmm_beta": [2], "both": [0, 1]}[args.kind]
     import numpy as np
     rng = np.random.default_rng(args.seed)
     for kind in kinds:

@@ -56,11 +56,12 @@ def _tiles_for(M, N, cplx):
     return out
 
 
-def tile_for_width(w, cplx, cap=40):
+def tile_for_width(w, cplx, cap=40, min_lanes=1):
     """Register tile (T_M, T_N) for the square width w: the least padded
     work P T_M T_N / w^2 (a guarded FMA still costs its FP64 issue slot),
     then the larger tile (fewer loads per FMA), then the squarer one;
-    at most `cap` accumulator doubles and one CTA's threads."""
+    at most `cap` accumulator doubles, and at least `min_lanes` row lanes
+    (256 // P) per CTA.  None if no tile meets the limits."""
     best = None
     c = 2 if cplx else 1
     for tm in range(1, w + 1):
@@ -68,28 +69,32 @@ def tile_for_width(w, cplx, cap=40):
             if tm * tn * c > cap:
                 continue
             P = math.ceil(w / tm) * math.ceil(w / tn)
-            if P > BLOCK:
+            if P > BLOCK // min_lanes:
                 continue
             waste = P * tm * tn / (w * w)
             key = (round(waste, 6), -tm * tn, abs(math.log2(tm) - math.log2(tn)), -tm)
             if best is None or key < best[0]:
                 best = (key, tm, tn)
-    return best[1], best[2]
+    return None if best is None else (best[1], best[2])
+
+
+def tpr_options(N, cplx, k=2):
+    """Up to k TSMM (threads per row t, results per thread npt) choices for
+    N columns: the least padding npt t - N, then npt closest to 4 (the
+    measured optimum of the tuned widths), then the larger npt."""
+    opts = []
+    for npt in range(1, (8 if cplx else 16) + 1):
+        t = math.ceil(N / npt)
+        if t > 64 or any(o[1] == t for o in opts):
+            continue
+        opts.append(((npt * t - N, abs(npt - 4), -npt), t, npt))
+    opts.sort()
+    return [(t, npt) for _, t, npt in opts[:k]]
 
 
 def tpr_for_width(N, cplx):
-    """TSMM threads per row t and results per thread npt for N columns: the
-    least padding npt t - N, then npt closest to 4 (the measured optimum of
-    the tuned widths), then the larger npt."""
-    best = None
-    for npt in range(1, (8 if cplx else 16) + 1):
-        t = math.ceil(N / npt)
-        if t > 64:
-            continue
-        key = (npt * t - N, abs(npt - 4), -npt)
-        if best is None or key < best[0]:
-            best = (key, t, npt)
-    return best[1], best[2]
+    """The first of tpr_options: (threads per row, results per thread)."""
+    return tpr_options(N, cplx, 1)[0]
 
 
 def default_specs():
@@ -103,15 +108,31 @@ def default_specs():
     # one width-specialised kernel per product for every other square width
     # (every w in 1..64 has a kernel without padding, or with at most a few
     # per cent of it, as the paper's generator does for each size, Sec. 2.1)
+    # Two or three candidates per width for the tuner: the least-padded
+    # tile, the same tile with two rows in flight per thread (U = 2) when its
+    # accumulators leave room, and, when the least-padded tile leaves a
+    # single row lane per CTA, the best tile with at least two; for TSMM the
+    # two best thread counts per row.
     for cplx in (False, True):
+        c = 2 if cplx else 1
         for w in range(1, 65):
             if w in SWEEP_SQUARE:
                 continue
+            tiles = []
             tm, tn = tile_for_width(w, cplx)
             U = 4 if tm * tn <= 2 else (2 if tm * tn <= 8 else 1)
-            tsmttsm.append(dict(cplx=cplx, M=w, N=w, TM=tm, TN=tn, U=U))
-            tpr, npt = tpr_for_width(w, cplx)
-            tsmm.append(dict(cplx=cplx, M=w, N=w, TPR=tpr, U=2 if npt * (2 if cplx else 1) <= 8 else 1))
+            tiles.append((tm, tn, U))
+            if U == 1 and tm * tn * c <= 24:
+                tiles.append((tm, tn, 2))
+            P = math.ceil(w / tm) * math.ceil(w / tn)
+            if BLOCK // P < 2:
+                t2 = tile_for_width(w, cplx, min_lanes=2)
+                if t2 is not None and t2 != (tm, tn):
+                    tiles.append((t2[0], t2[1], 4 if t2[0] * t2[1] <= 2 else (2 if t2[0] * t2[1] <= 8 else 1)))
+            for (a, b, u) in tiles:
+                tsmttsm.append(dict(cplx=cplx, M=w, N=w, TM=a, TN=b, U=u))
+            for tpr, npt in tpr_options(w, cplx, 2):
+                tsmm.append(dict(cplx=cplx, M=w, N=w, TPR=tpr, U=2 if npt * c <= 8 else 1))
     tshapes = [(w, w) for w in SWEEP_SQUARE] + list(TSMM_OFFDIAG)
     for cplx in (False, True):
         for (M, N) in tshapes:
@@ -278,7 +299,8 @@ def emit_tsmm(s):
             for c in range(CC):
                 w("        double x%d_%d_%d = 0.0, o%d_%d_%d = 0.0;" % (u, j, c, u, j, c))
     # beta != 0: the old B values are loaded before the FMAs, so their
-    # latency overlaps them instead of stalling the stores
+    # latency overlaps them instead of stalling the stores, and the beta
+    # term opens each FMA chain (no extra FP64 operation for beta = 1)
     w("        if (!a.beta_zero) {")
     for u in range(U):
         w("            if (rok%d) {" % u)
@@ -288,6 +310,8 @@ def emit_tsmm(s):
             w("                %s{" % guard)
             for c in range(CC):
                 w("                    o%d_%d_%d = bo[(q + %d) * %d + %d];" % (u, j, c, j * TPR, CC, c))
+            w("                    tsmm_acc_init<%d>(a, o%d_%d_0, o%d_%d_%d, x%d_%d_0, x%d_%d_%d);"
+              % (CC, u, j, u, j, CC - 1, u, j, u, j, CC - 1))
             w("                }")
         w("            }")
     w("        }")
@@ -314,8 +338,8 @@ def emit_tsmm(s):
         w("            double* out = a.B + (base + %d) * sb;" % (u * RPC))
         for j in range(NPT):
             guard = ("if (gn%d) " % j) if gn[j] else ""
-            w("            %stsmm_store_old<%d>(a, out, q + %d, x%d_%d_0, x%d_%d_%d, o%d_%d_0, o%d_%d_%d);"
-              % (guard, CC, j * TPR, u, j, u, j, CC - 1, u, j, u, j, CC - 1))
+            w("            %stsmm_store_plain<%d>(out, q + %d, x%d_%d_0, x%d_%d_%d);"
+              % (guard, CC, j * TPR, u, j, u, j, CC - 1))
         w("        }")
     w("    }")
     w("}")

@@ -124,7 +124,7 @@ static const Registry& registry() {
 
 static const std::vector<Variant>* table(tsm_kind kind) {
     if (kind == TSM_KIND_TSMTTSM) return &registry().tsmttsm;
-    if (kind == TSM_KIND_TSMM) return &registry().tsmm;
+    if (kind == TSM_KIND_TSMM || kind == TSM_KIND_TSMM_BETA) return &registry().tsmm;
     return nullptr;
 }
 
@@ -214,9 +214,13 @@ tsm_status choose(tsm_kind kind, int dtype, int M, int N, int64_t K, int* varian
     const std::vector<Variant>* t = table(kind);
     if (!t) return TSM_ERR_INVALID_VALUE;
     int v = -1, g = 0;
-    if (tune_lookup(kind, dtype, M, N, K, &v, &g) != TSM_OK || v < 0 || v >= (int)t->size() ||
-        !variant_supports((*t)[v], dtype, M, N)) {
-        v = heuristic_variant(kind, dtype, M, N);
+    auto looked_up = [&](tsm_kind k) {
+        return tune_lookup(k, dtype, M, N, K, &v, &g) == TSM_OK && v >= 0 && v < (int)t->size() &&
+               variant_supports((*t)[v], dtype, M, N);
+    };
+    // TSMM with beta != 0: its own entry first, else the beta = 0 one
+    if (!looked_up(kind) && !(kind == TSM_KIND_TSMM_BETA && looked_up(TSM_KIND_TSMM))) {
+        v = heuristic_variant(kind == TSM_KIND_TSMM_BETA ? TSM_KIND_TSMM : kind, dtype, M, N);
         g = 0;
     }
     if (v < 0) return TSM_ERR_NOT_SUPPORTED;
@@ -310,7 +314,7 @@ tsm_status run_tsmttsm(tsm_op opA, tsm_dtype dtype, int M, int N, int64_t K, con
     a.conj = (cplx && opA == TSM_OP_C) ? 1 : 0;
     a.ws = ws->partials;
     a.ticket = ws->tickets;
-    a.final_pass = (int64_t)g * M * N * (cplx ? 2 : 1) > kFinalThreshold ? 1 : 0;
+    a.final_pass = tsm_tsmttsm_kernels_per_call(dtype, M, N, g) == 2 ? 1 : 0;
     if (var.tsmttsm(a, g, stream) != cudaSuccess) return TSM_ERR_LAUNCH;
     if (a.final_pass && launch_tsmttsm_final(a, g, cplx, stream) != cudaSuccess) return TSM_ERR_LAUNCH;
     return TSM_OK;
@@ -340,7 +344,8 @@ tsm_status run_tsmm(tsm_op opC, tsm_dtype dtype, int M, int N, int64_t K, const 
     int v = variant, g = grid;
     if (v < 0) {
         int gg = 0;
-        if ((st = choose(TSM_KIND_TSMM, dtype, M, N, K, &v, &gg)) != TSM_OK) return st;
+        const tsm_kind key = beta_zero ? TSM_KIND_TSMM : TSM_KIND_TSMM_BETA;
+        if ((st = choose(key, dtype, M, N, K, &v, &gg)) != TSM_OK) return st;
         if (g <= 0) g = gg;
     }
     if (!supports(TSM_KIND_TSMM, v, dtype, M, N)) return TSM_ERR_NOT_SUPPORTED;
@@ -362,6 +367,7 @@ tsm_status run_tsmm(tsm_op opC, tsm_dtype dtype, int M, int N, int64_t K, const 
     a.beta_r = beta[0];
     a.beta_i = cplx ? beta[1] : 0.0;
     a.beta_zero = beta_zero;
+    a.beta_one = beta[0] == 1.0 && (!cplx || beta[1] == 0.0);
     if (var.tsmm(a, g, stream) != cudaSuccess) return TSM_ERR_LAUNCH;
     return TSM_OK;
 }
@@ -450,9 +456,15 @@ tsm_status tsm_variant_shape(tsm_kind kind, int index, tsm_dtype dtype, int M, i
     if (!variant_supports(*v, dtype, M, N)) return TSM_ERR_NOT_SUPPORTED;
     *info = v->info;
     if (v->info.runtime_tile) {
-        if (kind == TSM_KIND_TSMM) rt_tsmm_tpr(N, v->info.tile_n, &info->threads_per_row, &info->tile_n);
+        if (kind == TSM_KIND_TSMM || kind == TSM_KIND_TSMM_BETA)
+            rt_tsmm_tpr(N, v->info.tile_n, &info->threads_per_row, &info->tile_n);
     }
     return TSM_OK;
+}
+
+int tsm_tsmttsm_kernels_per_call(tsm_dtype dtype, int M, int N, int grid) {
+    if (M < 1 || N < 1 || M > 64 || N > 64 || grid < 1 || (dtype != TSM_R64 && dtype != TSM_C64)) return -1;
+    return (int64_t)grid * M * N * (dtype == TSM_C64 ? 2 : 1) > kFinalThreshold ? 2 : 1;
 }
 
 int tsm_variant_supports(tsm_kind kind, int index, tsm_dtype dtype, int M, int N) {

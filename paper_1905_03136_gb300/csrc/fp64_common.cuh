@@ -248,37 +248,50 @@ __device__ __forceinline__ void tsmttsm_finish(const TsmttsmArgs& a, const doubl
     if (t == 0) *a.ticket = 0u;
 }
 
-// TSMM output store: B[row][n] = acc (+ beta * B[row][n] unless beta == 0).
+// Starting value of a TSMM accumulator for B[row][n] whose old value (or,
+// oi) was loaded earlier: 0 when beta == 0, the old value itself when beta
+// == 1, beta * old otherwise.  The beta term thus opens the FMA chain
+// instead of costing an extra FP64 operation after it (none at all for
+// beta = 1), which matters on a part whose FP64 pipe is the bound.  For
+// real data (CC == 1) xi is not written: callers may pass xr's variable.
+// The general-beta products are volatile asm so that the compiler keeps
+// the branch: if-converted, the multiply would run for beta == 1 as well
+// (an extra FP64 operation per output on the bound pipe).
+__device__ __forceinline__ double dmul_kept(double x, double y) {
+    double r;
+    asm volatile("mul.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(x), "d"(y));
+    return r;
+}
+__device__ __forceinline__ double dfma_kept(double x, double y, double z) {
+    double r;
+    asm volatile("fma.rn.f64 %0, %1, %2, %3;" : "=d"(r) : "d"(x), "d"(y), "d"(z));
+    return r;
+}
+
 template <int CC>
-__device__ __forceinline__ void tsmm_store(const TsmmArgs& a, double* out, int n, double vr, double vi) {
-    if (CC == 1) {
-        if (!a.beta_zero) vr = fma(a.beta_r, out[n], vr);
-        out[n] = vr;
+__device__ __forceinline__ void tsmm_acc_init(const TsmmArgs& a, double orr, double oi, double& xr, double& xi) {
+    if (a.beta_zero) {
+        xr = 0.0;
+        if (CC == 2) xi = 0.0;
+    } else if (a.beta_one) {
+        xr = orr;
+        if (CC == 2) xi = oi;
+    } else if (CC == 1) {
+        xr = dmul_kept(a.beta_r, orr);
     } else {
-        if (!a.beta_zero) {
-            const double orr = out[n * 2], oi = out[n * 2 + 1];
-            vr += a.beta_r * orr - a.beta_i * oi;
-            vi += a.beta_r * oi + a.beta_i * orr;
-        }
-        out[n * 2] = vr;
-        out[n * 2 + 1] = vi;
+        const double nr = dfma_kept(a.beta_r, orr, -dmul_kept(a.beta_i, oi));
+        const double ni = dfma_kept(a.beta_r, oi, dmul_kept(a.beta_i, orr));
+        xr = nr;
+        xi = ni;
     }
 }
 
-// As tsmm_store, with the old B[row][n] (or, ob) loaded earlier, together
-// with the row's A values, so that its latency overlaps the FMAs instead of
-// stalling the store (only read when beta != 0).
+// TSMM output store of a finished accumulator (beta already folded in).
 template <int CC>
-__device__ __forceinline__ void tsmm_store_old(const TsmmArgs& a, double* out, int n, double vr, double vi,
-                                               double orr, double oi) {
+__device__ __forceinline__ void tsmm_store_plain(double* out, int n, double vr, double vi) {
     if (CC == 1) {
-        if (!a.beta_zero) vr = fma(a.beta_r, orr, vr);
         out[n] = vr;
     } else {
-        if (!a.beta_zero) {
-            vr += a.beta_r * orr - a.beta_i * oi;
-            vi += a.beta_r * oi + a.beta_i * orr;
-        }
         out[n * 2] = vr;
         out[n * 2 + 1] = vi;
     }

@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(kBlock) k_tsmm(const TsmmArgs a) {
 #pragma unroll
                 for (int c = 0; c < CC; ++c) acc[u][j][c] = ob[u][j][c] = 0.0;
         if (!a.beta_zero) {
-            // old B values first, so their latency overlaps the FMAs
+            // old B values first, so their latency overlaps the FMAs; the
+            // beta term then opens each FMA chain (tsmm_acc_init)
 #pragma unroll
             for (int u = 0; u < U; ++u)
 #pragma unroll
@@ -74,6 +75,7 @@ __global__ void __launch_bounds__(kBlock) k_tsmm(const TsmmArgs a) {
                     if (rok[u] && n < N)
 #pragma unroll
                         for (int c = 0; c < CC; ++c) ob[u][j][c] = a.B[row[u] * sb + n * CC + c];
+                    tsmm_acc_init<CC>(a, ob[u][j][0], ob[u][j][CC - 1], acc[u][j][0], acc[u][j][CC - 1]);
                 }
         }
 #pragma unroll 2
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(kBlock) k_tsmm(const TsmmArgs a) {
                 if (j >= npt) break;
                 const int n = q + j * TPR;
                 if (n >= N) continue;
-                tsmm_store_old<CC>(a, out, n, acc[u][j][0], acc[u][j][CC - 1], ob[u][j][0], ob[u][j][CC - 1]);
+                tsmm_store_plain<CC>(out, n, acc[u][j][0], acc[u][j][CC - 1]);
             }
         }
     }

@@ -371,11 +371,13 @@ __global__ void __launch_bounds__(kBlock) k_tsmm_narrow(const TsmmArgs a, int ve
     const int64_t G = gridDim.x, b = blockIdx.x;
     const bool bz = a.beta_zero != 0;
 
-    // out[n*CC + c] = sum_m in[m] * cr[m][n] (+ beta * old)
+    // out[n*CC + c] = sum_m in[m] * cr[m][n] (+ beta * old, which opens the
+    // FMA chain: no extra FP64 operation for beta = 1)
     auto row_out = [&](const double* in, const double* old, double* out) {
 #pragma unroll
         for (int n = 0; n < N; ++n) {
             double xr = 0.0, xi = 0.0;
+            if (!bz) tsmm_acc_init<CC>(a, old[n * CC], old[n * CC + CC - 1], xr, xi);
 #pragma unroll
             for (int m = 0; m < M; ++m) {
                 if (CC == 1) {
@@ -390,14 +392,8 @@ __global__ void __launch_bounds__(kBlock) k_tsmm_narrow(const TsmmArgs a, int ve
                 }
             }
             if (CC == 1) {
-                if (!bz) xr = fma(a.beta_r, old[n], xr);
                 out[n] = xr;
             } else {
-                if (!bz) {
-                    const double orr = old[2 * n], oi = old[2 * n + 1];
-                    xr += a.beta_r * orr - a.beta_i * oi;
-                    xi += a.beta_r * oi + a.beta_i * orr;
-                }
                 out[2 * n] = xr;
                 out[2 * n + 1] = xi;
             }

@@ -43,6 +43,7 @@ struct TsmmArgs {
     int64_t ldb;
     double alpha_r, alpha_i, beta_r, beta_i;
     int beta_zero;
+    int beta_one;     // beta == 1 exactly: the old B value starts the FMA chain as it is
 };
 
 typedef cudaError_t (*TsmttsmLaunch)(const TsmttsmArgs&, int grid, cudaStream_t);

@@ -185,10 +185,12 @@ tsm_status tsm_time_variant(tsm_kind kind, tsm_dtype dtype, int M, int N, int64_
     if (!supports(kind, variant, dtype, M, N)) return TSM_ERR_NOT_SUPPORTED;
     const double one[2] = {1.0, 0.0}, zero[2] = {0.0, 0.0};
     cudaStream_t s = (cudaStream_t)stream;
+    // TSM_KIND_TSMM_BETA: the TSMM variants with beta = 1 (B is read too)
+    const double* beta = kind == TSM_KIND_TSMM_BETA ? one : zero;
     auto run = [&]() -> tsm_status {
         if (kind == TSM_KIND_TSMTTSM)
             return run_tsmttsm(TSM_OP_T, dtype, M, N, K, one, X, ldx, Y, ldy, zero, Z, ldz, variant, grid, s);
-        return run_tsmm(TSM_OP_N, dtype, M, N, K, one, X, ldx, Y, ldy, zero, Z, ldz, variant, grid, s);
+        return run_tsmm(TSM_OP_N, dtype, M, N, K, one, X, ldx, Y, ldy, beta, Z, ldz, variant, grid, s);
     };
     tsm_status st = run();  // warm-up (also grows the workspace)
     if (st != TSM_OK) return st;

@@ -58,6 +58,19 @@ def test_binding_covers_declared_functions(lib):
     assert not missing, "no Python binding for: %s" % sorted(missing)
 
 
+def test_kernels_per_call_rule(lib):
+    """One launch per TSMTTSM call, two when grid * M * N * c CTA partial
+    doubles exceed 32768 (the final reduction pass); -1 for bad shapes."""
+    import paper_1905_03136_gb300 as t
+    assert lib.tsm_tsmttsm_kernels_per_call(t.R64, 1, 1, 304) == 1
+    assert lib.tsm_tsmttsm_kernels_per_call(t.R64, 16, 16, 128) == 1      # 32768: not above
+    assert lib.tsm_tsmttsm_kernels_per_call(t.R64, 16, 16, 129) == 2
+    assert lib.tsm_tsmttsm_kernels_per_call(t.C64, 64, 64, 152) == 2
+    assert lib.tsm_tsmttsm_kernels_per_call(t.C64, 8, 8, 256) == 1       # 32768 complex doubles
+    for bad in ((0, 1, 1), (65, 1, 1), (1, 1, 0)):
+        assert lib.tsm_tsmttsm_kernels_per_call(t.R64, bad[0], bad[1], bad[2]) == -1
+
+
 def test_status_strings(lib):
     for s in range(8):
         assert lib.tsm_status_string(s)
@@ -77,6 +90,8 @@ def test_variant_table(lib):
     info = t.VariantInfo()
     assert lib.tsm_variant_get(0, 10 ** 6, ctypes.byref(info)) == 1
     assert lib.tsm_variant_count(7) == -1
+    # the TSMM-with-beta tuning key names the TSMM variants
+    assert lib.tsm_variant_count(t.KIND_TSMM_BETA) == lib.tsm_variant_count(t.KIND_TSMM)
 
 
 def test_generic_variant_supports_every_shape(lib):

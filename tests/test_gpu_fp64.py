@@ -152,6 +152,7 @@ def test_tsmm_every_variant(tsm, shape, cplx):
     alpha, beta = (1.5 + 0.5j, -0.5 + 1j) if cplx else (1.5, -0.5)
     ref0 = oracle.apply(A, Cm)
     ref1 = oracle.apply(A, Cm, alpha, beta, B0)
+    ref2 = oracle.apply(A, Cm, alpha, 1.0, B0)
     vs = _variants_for(tsm, tsm.KIND_TSMM, dt, M, N)
     assert vs
     for v in vs:
@@ -163,6 +164,11 @@ def test_tsmm_every_variant(tsm, shape, cplx):
         tsm.tsmm(dA, dC, dB, alpha, beta, variant=v)
         err = oracle.rel_fro(host(dB), ref1)
         assert err <= TOL, (tsm.variants(tsm.KIND_TSMM)[v]["name"], "alpha/beta", err)
+        # beta = 1 exactly: the old B value opens the FMA chain unscaled
+        dB = dev(B0)
+        tsm.tsmm(dA, dC, dB, alpha, 1.0, variant=v)
+        err = oracle.rel_fro(host(dB), ref2)
+        assert err <= TOL, (tsm.variants(tsm.KIND_TSMM)[v]["name"], "beta = 1", err)
 
 
 @pytest.mark.parametrize("cplx", [False, True], ids=["r64", "c64"])
@@ -303,13 +309,52 @@ def test_every_width_fixed_shape_kernels(tsm, cplx):
             seen += 1
         ref0 = oracle.apply(A, Cm)
         ref1 = oracle.apply(A, Cm, alpha, beta, B)
+        ref2 = oracle.apply(A, Cm, 1.0, 1.0, B)
         for v in fixed_m:
             assert oracle.rel_fro(host(tsm.tsmm(dA, dC, variant=v)), ref0) <= TOL, (mv[v]["name"], w)
             out = dev(B)
             tsm.tsmm(dA, dC, out, alpha, beta, variant=v)
             assert oracle.rel_fro(host(out), ref1) <= TOL, (mv[v]["name"], w, "beta")
+            out = dev(B)
+            tsm.tsmm(dA, dC, out, 1.0, 1.0, variant=v)
+            assert oracle.rel_fro(host(out), ref2) <= TOL, (mv[v]["name"], w, "beta = 1")
             seen += 1
     assert seen >= 127
+
+
+def test_tsmm_beta_tuning_key(tsm, tmp_path):
+    """TSMM with beta != 0 has a tuning key of its own: tsm_tune with kind
+    TSMM_BETA times the TSMM variants with beta = 1 and records the winner
+    under that key, tsm_choose returns it for that key, and calls with
+    beta != 0 still match the oracle.  The loaded table is restored."""
+    import ctypes
+    from paper_1905_03136_gb300 import _lib
+    lib = tsm.load()
+    saved = str(tmp_path / "table.txt").encode()
+    _lib.call("tsm_save_tuning", saved)
+    try:
+        lib.tsm_clear_tuning()
+        K, M, N = 70001, 3, 3
+        A = synth.block_vector(81, K, M)
+        Cm = synth.small_matrix(82, M, N)
+        B0 = synth.block_vector(83, K, N)
+        dA, dC = dev(A), dev(Cm)
+        Z = dev(B0)
+        samples = tsm.tune(tsm.KIND_TSMM_BETA, dA, dC, Z, reps=1)
+        assert samples
+        best = min(samples, key=lambda s: s[2])
+        assert tsm.choose(tsm.KIND_TSMM_BETA, tsm.R64, M, N, K) == (best[0], best[1])
+        # the search wrote its own key (2) and no beta = 0 entry (1)
+        after = str(tmp_path / "after.txt")
+        _lib.call("tsm_save_tuning", after.encode())
+        keys = [tuple(int(x) for x in line.split()[:4]) for line in open(after) if not line.startswith("#")]
+        assert (2, 0, M, N) in keys and (1, 0, M, N) not in keys
+        out = dev(B0)
+        tsm.tsmm(dA, dC, out, 1.5, -0.5)
+        assert oracle.rel_fro(host(out), oracle.apply(A, Cm, 1.5, -0.5, B0)) <= TOL
+    finally:
+        lib.tsm_clear_tuning()
+        _lib.call("tsm_load_tuning", saved)
 
 
 def test_device_fill_matches_host_generator(tsm):
