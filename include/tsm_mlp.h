@@ -7,7 +7,7 @@
  * characteristics instead (Sec. 7).  This is that model's network.  It maps
  * a feature vector describing (shape, kernel variant, launch) to a predicted
  * cost; the tuner evaluates it for every candidate of an unseen shape and
- * keeps the argmin, with exhaustive search kept as its fallback and judge.
+ * keeps the argmin, with exhaustive search kept as its fallback and yardstick.
  *
  * Network:  h1 = tanh(W1 x + b1),  h2 = tanh(W2 h1 + b2),  y = w3 . h2 + b3
  * with x in R^D (D <= TSM_MLP_MAX_IN), hidden width H (<= 64), scalar y.

@@ -10,7 +10,7 @@ kernels) learns, from the autotuner's timing log, the function
 i.e. how far a configuration stays from the roofline bound of Eq. 1.  For an
 unseen shape it scores every candidate the exhaustive search would time
 (every supporting variant at the tuner's grid sizes) and keeps the argmin;
-exhaustive tuning remains the fallback and the judge of its regret.
+exhaustive tuning remains the fallback and the yardstick of its regret.
 """
 
 import json

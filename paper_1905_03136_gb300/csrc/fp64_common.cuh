@@ -249,42 +249,33 @@ __device__ __forceinline__ void tsmttsm_finish(const TsmttsmArgs& a, const doubl
 }
 
 // Starting value of a TSMM accumulator for B[row][n] whose old value (or,
-// oi) was loaded earlier: 0 when beta == 0, the old value itself when beta
-// == 1, beta * old otherwise.  The beta term thus opens the FMA chain
-// instead of costing an extra FP64 operation after it (none at all for
-// beta = 1), which matters on a part whose FP64 pipe is the bound.  For
-// real data (CC == 1) xi is not written: callers may pass xr's variable.
-// The general-beta products are volatile asm so that the compiler keeps
-// the branch: if-converted, the multiply would run for beta == 1 as well
-// (an extra FP64 operation per output on the bound pipe).
-__device__ __forceinline__ double dmul_kept(double x, double y) {
-    double r;
-    asm volatile("mul.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(x), "d"(y));
-    return r;
-}
-__device__ __forceinline__ double dfma_kept(double x, double y, double z) {
-    double r;
-    asm volatile("fma.rn.f64 %0, %1, %2, %3;" : "=d"(r) : "d"(x), "d"(y), "d"(z));
-    return r;
-}
-
-template <int CC>
+// oi) was loaded earlier.  GEN = false serves beta == 0 (start at 0) and
+// beta == 1 (start at the old value itself): selects only, no FP64
+// operation.  GEN = true serves any other beta (start at beta * old).  The
+// beta term thus opens the FMA chain instead of costing an FP64 operation
+// after it, and the two cases are separate kernel instantiations: with one
+// code path for all betas the compiler would run the beta * old multiply
+// for beta == 1 too (if-converted), an extra FP64 operation per output on
+// the pipe that bounds these kernels.  For real data (CC == 1) xi is not
+// written: callers may pass xr's variable.
+template <int CC, bool GEN>
 __device__ __forceinline__ void tsmm_acc_init(const TsmmArgs& a, double orr, double oi, double& xr, double& xi) {
-    if (a.beta_zero) {
-        xr = 0.0;
-        if (CC == 2) xi = 0.0;
-    } else if (a.beta_one) {
-        xr = orr;
-        if (CC == 2) xi = oi;
+    if (!GEN) {
+        xr = a.beta_zero ? 0.0 : orr;
+        if (CC == 2) xi = a.beta_zero ? 0.0 : oi;
     } else if (CC == 1) {
-        xr = dmul_kept(a.beta_r, orr);
+        xr = a.beta_r * orr;
     } else {
-        const double nr = dfma_kept(a.beta_r, orr, -dmul_kept(a.beta_i, oi));
-        const double ni = dfma_kept(a.beta_r, oi, dmul_kept(a.beta_i, orr));
+        const double nr = fma(a.beta_r, orr, -a.beta_i * oi);
+        const double ni = fma(a.beta_r, oi, a.beta_i * orr);
         xr = nr;
         xi = ni;
     }
 }
+
+// Host side: a beta other than 0 and 1 takes the instantiation that scales
+// the old B values (GEN = true above).
+inline bool tsmm_general_beta(const TsmmArgs& a) { return !a.beta_zero && !a.beta_one; }
 
 // TSMM output store of a finished accumulator (beta already folded in).
 template <int CC>

@@ -34,7 +34,7 @@ namespace {
 
 // --------------------------------------------------------------------- TSMM
 
-template <int TPR, int NPT, int U, bool CPLX>
+template <int TPR, int NPT, int U, bool CPLX, bool GEN>
 __global__ void __launch_bounds__(kBlock) k_tsmm(const TsmmArgs a) {
     constexpr int CC = CPLX ? 2 : 1;
     constexpr int RPC = kBlock / TPR;  // rows per CTA per unrolled step
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kBlock) k_tsmm(const TsmmArgs a) {
                     if (rok[u] && n < N)
 #pragma unroll
                         for (int c = 0; c < CC; ++c) ob[u][j][c] = a.B[row[u] * sb + n * CC + c];
-                    tsmm_acc_init<CC>(a, ob[u][j][0], ob[u][j][CC - 1], acc[u][j][0], acc[u][j][CC - 1]);
+                    tsmm_acc_init<CC, GEN>(a, ob[u][j][0], ob[u][j][CC - 1], acc[u][j][0], acc[u][j][CC - 1]);
                 }
         }
 #pragma unroll 2
@@ -129,16 +129,22 @@ size_t tsmm_smem(int M, int N) {
     return (size_t)M * N * (CPLX ? 2 : 1) * sizeof(double);
 }
 
-template <int TPR, int NPT, int U, bool CPLX>
-cudaError_t launch_tsmm(const TsmmArgs& a, int grid, cudaStream_t s) {
+template <int TPR, int NPT, int U, bool CPLX, bool GEN>
+cudaError_t launch_tsmm_as(const TsmmArgs& a, int grid, cudaStream_t s) {
     const size_t smem = tsmm_smem<TPR, NPT, U, CPLX>(a.M, a.N);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_tsmm<TPR, NPT, U, CPLX>,
+        cudaError_t e = cudaFuncSetAttribute(k_tsmm<TPR, NPT, U, CPLX, GEN>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_tsmm<TPR, NPT, U, CPLX><<<grid, kBlock, smem, s>>>(a);
+    k_tsmm<TPR, NPT, U, CPLX, GEN><<<grid, kBlock, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <int TPR, int NPT, int U, bool CPLX>
+cudaError_t launch_tsmm(const TsmmArgs& a, int grid, cudaStream_t s) {
+    return tsmm_general_beta(a) ? launch_tsmm_as<TPR, NPT, U, CPLX, true>(a, grid, s)
+                                : launch_tsmm_as<TPR, NPT, U, CPLX, false>(a, grid, s);
 }
 
 template <int TPR, int NPT, int U, bool CPLX>
@@ -146,11 +152,11 @@ int occ_tsmm(int M, int N) {
     if (N > TPR * NPT) return 0;
     const size_t smem = tsmm_smem<TPR, NPT, U, CPLX>(M, N);
     if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(k_tsmm<TPR, NPT, U, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_tsmm<TPR, NPT, U, CPLX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tsmm<TPR, NPT, U, CPLX>, kBlock, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tsmm<TPR, NPT, U, CPLX, false>, kBlock, smem) !=
         cudaSuccess)
         return 0;
     return n;

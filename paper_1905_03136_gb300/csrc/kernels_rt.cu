@@ -47,7 +47,7 @@ namespace {
 
 // --------------------------------------------------------------------- TSMM
 
-template <int NPT, int U, bool CPLX>
+template <int NPT, int U, bool CPLX, bool GEN>
 __global__ void __launch_bounds__(kBlock) k_tsmm_rt(const TsmmArgs a, const int tpr) {
     constexpr int CC = CPLX ? 2 : 1;
     extern __shared__ double cs[];  // alpha * C, M x N (x CC)
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kBlock) k_tsmm_rt(const TsmmArgs a, const int 
                     if (rok[u] && n < N)
 #pragma unroll
                         for (int c = 0; c < CC; ++c) ob[u][j][c] = a.B[row[u] * sb + n * CC + c];
-                    tsmm_acc_init<CC>(a, ob[u][j][0], ob[u][j][CC - 1], acc[u][j][0], acc[u][j][CC - 1]);
+                    tsmm_acc_init<CC, GEN>(a, ob[u][j][0], ob[u][j][CC - 1], acc[u][j][0], acc[u][j][CC - 1]);
                 }
         }
         if (live) {
@@ -138,29 +138,35 @@ __global__ void __launch_bounds__(kBlock) k_tsmm_rt(const TsmmArgs a, const int 
     }
 }
 
-template <int NPT, int U, bool CPLX>
-cudaError_t launch_tsmm_rt(const TsmmArgs& a, int grid, cudaStream_t s) {
+template <int NPT, int U, bool CPLX, bool GEN>
+cudaError_t launch_tsmm_rt_as(const TsmmArgs& a, int grid, cudaStream_t s) {
     int tpr = 1, npt = 1;
     rt_tsmm_tpr(a.N, NPT, &tpr, &npt);
     const size_t smem = (size_t)a.M * a.N * (CPLX ? 2 : 1) * sizeof(double);
     if (smem > 48 * 1024) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_tsmm_rt<NPT, U, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_tsmm_rt<NPT, U, CPLX, GEN>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_tsmm_rt<NPT, U, CPLX><<<grid, kBlock, smem, s>>>(a, tpr);
+    k_tsmm_rt<NPT, U, CPLX, GEN><<<grid, kBlock, smem, s>>>(a, tpr);
     return cudaGetLastError();
+}
+
+template <int NPT, int U, bool CPLX>
+cudaError_t launch_tsmm_rt(const TsmmArgs& a, int grid, cudaStream_t s) {
+    return tsmm_general_beta(a) ? launch_tsmm_rt_as<NPT, U, CPLX, true>(a, grid, s)
+                                : launch_tsmm_rt_as<NPT, U, CPLX, false>(a, grid, s);
 }
 
 template <int NPT, int U, bool CPLX>
 int occ_tsmm_rt(int M, int N) {
     const size_t smem = (size_t)M * N * (CPLX ? 2 : 1) * sizeof(double);
     if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(k_tsmm_rt<NPT, U, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaFuncSetAttribute(k_tsmm_rt<NPT, U, CPLX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
         return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tsmm_rt<NPT, U, CPLX>, kBlock, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tsmm_rt<NPT, U, CPLX, false>, kBlock, smem) != cudaSuccess)
         return 0;
     return n;
 }
