@@ -278,7 +278,13 @@ def emit_tsmm(s):
     gn = [(TPR - 1) + j * TPR >= N for j in range(NPT)]
     o = []
     w = o.append
-    w("template <bool GEN>")
+    # Kernels with at most 8 threads per row are instantiated twice, for beta
+    # in {0, 1} and for any other beta (tsmm_acc_init); the others keep one
+    # instantiation (tsmm_acc_init_kept): measured side by side, the split
+    # helped the former and slowed the latter.
+    split = TPR <= 8
+    if split:
+        w("template <bool GEN>")
     w("__global__ void __launch_bounds__(%d) %s(const TsmmArgs a) {" % (BLOCK, name))
     w("    extern __shared__ double cs[];")
     w("    tsmm_stage_c<%d>(a, cs);" % CC)
@@ -311,8 +317,9 @@ def emit_tsmm(s):
             w("                %s{" % guard)
             for c in range(CC):
                 w("                    o%d_%d_%d = bo[(q + %d) * %d + %d];" % (u, j, c, j * TPR, CC, c))
-            w("                    tsmm_acc_init<%d, GEN>(a, o%d_%d_0, o%d_%d_%d, x%d_%d_0, x%d_%d_%d);"
-              % (CC, u, j, u, j, CC - 1, u, j, u, j, CC - 1))
+            w("                    %s(a, o%d_%d_0, o%d_%d_%d, x%d_%d_0, x%d_%d_%d);"
+              % (("tsmm_acc_init<%d, GEN>" if split else "tsmm_acc_init_kept<%d>") % CC,
+                 u, j, u, j, CC - 1, u, j, u, j, CC - 1))
             w("                }")
         w("            }")
     w("        }")
@@ -346,26 +353,34 @@ def emit_tsmm(s):
     w("}")
     w("")
     smem = M * N * CC * 8
-    # beta other than 0 and 1 takes the GEN = true instantiation
+    # with the split, a beta other than 0 and 1 takes GEN = true
+    base = name + "<false>" if split else name
     w("cudaError_t launch_%s(const TsmmArgs& a, int grid, cudaStream_t s) {" % name)
-    w("    const bool gen = tsmm_general_beta(a);")
-    if smem > 48 * 1024:
-        w("    cudaError_t e = cudaFuncSetAttribute(gen ? %s<true> : %s<false>, "
-          "cudaFuncAttributeMaxDynamicSharedMemorySize, %d);" % (name, name, smem))
-        w("    if (e != cudaSuccess) return e;")
-    w("    if (gen)")
-    w("        %s<true><<<grid, %d, %d, s>>>(a);" % (name, BLOCK, smem))
-    w("    else")
-    w("        %s<false><<<grid, %d, %d, s>>>(a);" % (name, BLOCK, smem))
+    if split:
+        w("    const bool gen = tsmm_general_beta(a);")
+        if smem > 48 * 1024:
+            w("    cudaError_t e = cudaFuncSetAttribute(gen ? %s<true> : %s<false>, "
+              "cudaFuncAttributeMaxDynamicSharedMemorySize, %d);" % (name, name, smem))
+            w("    if (e != cudaSuccess) return e;")
+        w("    if (gen)")
+        w("        %s<true><<<grid, %d, %d, s>>>(a);" % (name, BLOCK, smem))
+        w("    else")
+        w("        %s<false><<<grid, %d, %d, s>>>(a);" % (name, BLOCK, smem))
+    else:
+        if smem > 48 * 1024:
+            w("    cudaError_t e = cudaFuncSetAttribute(%s, cudaFuncAttributeMaxDynamicSharedMemorySize, %d);"
+              % (name, smem))
+            w("    if (e != cudaSuccess) return e;")
+        w("    %s<<<grid, %d, %d, s>>>(a);" % (name, BLOCK, smem))
     w("    return cudaGetLastError();")
     w("}")
     w("int occ_%s(int, int) {" % name)
     if smem > 48 * 1024:
-        w("    if (cudaFuncSetAttribute(%s<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, %d) != cudaSuccess)"
-          " return 0;" % (name, smem))
+        w("    if (cudaFuncSetAttribute(%s, cudaFuncAttributeMaxDynamicSharedMemorySize, %d) != cudaSuccess)"
+          " return 0;" % (base, smem))
     w("    int n = 0;")
-    w("    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, %s<false>, %d, %d) != cudaSuccess) return 0;"
-      % (name, BLOCK, smem))
+    w("    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, %s, %d, %d) != cudaSuccess) return 0;"
+      % (base, BLOCK, smem))
     w("    return n;")
     w("}")
     w("")

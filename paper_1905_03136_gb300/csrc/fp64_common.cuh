@@ -273,6 +273,42 @@ __device__ __forceinline__ void tsmm_acc_init(const TsmmArgs& a, double orr, dou
     }
 }
 
+// Single-instantiation form of tsmm_acc_init, for the kernels that are not
+// split by beta (the narrow kernels and the generated ones with more than
+// 8 threads per row): the general-beta products are volatile asm so that
+// the compiler keeps the branch (if-converted, the multiply would run for
+// beta == 1 as well).  Measured side by side, the split made those kernels
+// slower (their beta = 0 path by up to 60 %), and this form keeps beta = 1
+// free of FP64 multiplies without it.
+__device__ __forceinline__ double dmul_kept(double x, double y) {
+    double r;
+    asm volatile("mul.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(x), "d"(y));
+    return r;
+}
+__device__ __forceinline__ double dfma_kept(double x, double y, double z) {
+    double r;
+    asm volatile("fma.rn.f64 %0, %1, %2, %3;" : "=d"(r) : "d"(x), "d"(y), "d"(z));
+    return r;
+}
+
+template <int CC>
+__device__ __forceinline__ void tsmm_acc_init_kept(const TsmmArgs& a, double orr, double oi, double& xr, double& xi) {
+    if (a.beta_zero) {
+        xr = 0.0;
+        if (CC == 2) xi = 0.0;
+    } else if (a.beta_one) {
+        xr = orr;
+        if (CC == 2) xi = oi;
+    } else if (CC == 1) {
+        xr = dmul_kept(a.beta_r, orr);
+    } else {
+        const double nr = dfma_kept(a.beta_r, orr, -dmul_kept(a.beta_i, oi));
+        const double ni = dfma_kept(a.beta_r, oi, dmul_kept(a.beta_i, orr));
+        xr = nr;
+        xi = ni;
+    }
+}
+
 // Host side: a beta other than 0 and 1 takes the instantiation that scales
 // the old B values (GEN = true above).
 inline bool tsmm_general_beta(const TsmmArgs& a) { return !a.beta_zero && !a.beta_one; }

@@ -348,7 +348,7 @@ int occ_tsmttsm_narrow(int, int) {
 
 // ------------------------------------------------------------------ TSMM
 
-template <int M, int N, int CC, int VW, int U, bool PF, bool GEN>
+template <int M, int N, int CC, int VW, int U, bool PF>
 __global__ void __launch_bounds__(kBlock) k_tsmm_narrow(const TsmmArgs a, int vec) {
     typedef Group<M, N, CC, VW> Gp;
     constexpr int R = Gp::R, EA = Gp::EA, EB = Gp::EB;
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(kBlock) k_tsmm_narrow(const TsmmArgs a, int ve
 #pragma unroll
         for (int n = 0; n < N; ++n) {
             double xr = 0.0, xi = 0.0;
-            if (!bz) tsmm_acc_init<CC, GEN>(a, old[n * CC], old[n * CC + CC - 1], xr, xi);
+            if (!bz) tsmm_acc_init_kept<CC>(a, old[n * CC], old[n * CC + CC - 1], xr, xi);
 #pragma unroll
             for (int m = 0; m < M; ++m) {
                 if (CC == 1) {
@@ -531,17 +531,14 @@ template <int M, int N, int CC, int VW, int U, bool PF>
 cudaError_t launch_tsmm_narrow(const TsmmArgs& a, int grid, cudaStream_t s) {
     if (a.M != M || a.N != N) return cudaErrorInvalidValue;
     const int vec = narrow_vec_ok<M, N, CC, VW>(a.A, a.lda, a.B, a.ldb) ? 1 : 0;
-    if (tsmm_general_beta(a))
-        k_tsmm_narrow<M, N, CC, VW, U, PF, true><<<grid, kBlock, 0, s>>>(a, vec);
-    else
-        k_tsmm_narrow<M, N, CC, VW, U, PF, false><<<grid, kBlock, 0, s>>>(a, vec);
+    k_tsmm_narrow<M, N, CC, VW, U, PF><<<grid, kBlock, 0, s>>>(a, vec);
     return cudaGetLastError();
 }
 
 template <int M, int N, int CC, int VW, int U, bool PF>
 int occ_tsmm_narrow(int, int) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tsmm_narrow<M, N, CC, VW, U, PF, false>, kBlock, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tsmm_narrow<M, N, CC, VW, U, PF>, kBlock, 0) !=
         cudaSuccess)
         return 0;
     return n;
