@@ -71,6 +71,35 @@ def test_kernels_per_call_rule(lib):
         assert lib.tsm_tsmttsm_kernels_per_call(t.R64, bad[0], bad[1], bad[2]) == -1
 
 
+def test_timed_tuning_entry_round_trip(lib, tmp_path):
+    """tsm_set_tuning_timed records (variant, grid, ms) under its key and the
+    table file keeps them; a variant that cannot run the shape is refused.
+    Host-only table logic: no device needed.  The loaded table is restored."""
+    import paper_1905_03136_gb300 as t
+    from paper_1905_03136_gb300 import _lib
+    saved = str(tmp_path / "saved.txt").encode()
+    _lib.call("tsm_save_tuning", saved)
+    try:
+        lib.tsm_clear_tuning()
+        vs = t.variants(t.KIND_TSMTTSM)
+        gen = [v for v in vs if v["name"] == "gen_tsmttsm_r64_m37n37_t1x37_u1"
+               or (v["fixed_m"] == 37 and v["dtype"] == 0)]
+        assert gen, "no generated kernel for real width 37"
+        v = gen[0]
+        assert lib.tsm_set_tuning_timed(t.KIND_TSMTTSM, t.R64, 37, 37, 1 << 24, v["index"], 304,
+                                        ctypes.c_float(12.5)) == 0
+        # a kernel fixed to width 37 cannot run 36 x 36
+        assert lib.tsm_set_tuning_timed(t.KIND_TSMTTSM, t.R64, 36, 36, 1 << 24, v["index"], 304,
+                                        ctypes.c_float(1.0)) == 1
+        out = str(tmp_path / "t.txt")
+        _lib.call("tsm_save_tuning", out.encode())
+        lines = [l.split() for l in open(out) if not l.startswith("#")]
+        assert lines == [["0", "0", "37", "37", "24", v["name"], "304", "12.500000"]]
+    finally:
+        lib.tsm_clear_tuning()
+        _lib.call("tsm_load_tuning", saved)
+
+
 def test_status_strings(lib):
     for s in range(8):
         assert lib.tsm_status_string(s)
