@@ -412,7 +412,7 @@ def run_e2e(args, flatA, flatB, outs, views, ideal, dev, K):
     the C results go back to the host: the same metric measured end to end.
     Each configuration's inputs are copied in full (no reuse across calls);
     the copies of the next configurations overlap the current kernel through
-    a second stream and three device slots, and the 22 small results are read
+    a second stream and four device slots, and the 22 small results are read
     back behind the last product (a read-back after every call, on the
     compute stream, stalled the pipeline: one sweep took 2.7 s instead of
     1.4 s)."""
@@ -427,7 +427,7 @@ def run_e2e(args, flatA, flatB, outs, views, ideal, dev, K):
         pinned = False
     hA.copy_(flatA)
     hB.copy_(flatB)
-    nslot = 3  # device slots: the copies may run two calls ahead of the products
+    nslot = 4  # device slots: the copies may run three calls ahead of the products
     slots = [(torch.empty_like(flatA), torch.empty_like(flatB)) for _ in range(nslot)]
     hC = {cfg: torch.empty(outs[cfg].shape, dtype=outs[cfg].dtype, pin_memory=pinned) for cfg in SWEEP}
     import paper_1905_03136_gb300 as tsm
@@ -476,8 +476,8 @@ def run_e2e(args, flatA, flatB, outs, views, ideal, dev, K):
     return {"value": 100.0 * sum(ideal.values()) / secs, "unit": "% of roofline", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": secs * 1e3, "pinned": pinned,
             "h2d_gbs_single_copy": round(h2d_gbs, 1),
-            "note": "every call copies its own A and B (no reuse) on a copy stream running up to two calls "
-                    "ahead of the products (three device slots); the C results are read back at the end of the step"}
+            "note": "every call copies its own A and B (no reuse) on a copy stream running up to three calls "
+                    "ahead of the products (four device slots); the C results are read back at the end of the step"}
 
 
 # ------------------------------------------------------------------ extras
