@@ -5,6 +5,9 @@ leg may import this package.  The CUDA library never calls it, and it
 shares no code with the library: the products are computed by the plain C
 file ``tsm_oracle.c`` (the definition of Sec. 1.1 / Listing 1 written out
 in binary64 with compensated summation), compiled here with gcc.
+``tsm_plain.c`` holds both products as plain uncompensated loops, threaded
+over K: the timed CPU baseline (``tsmttsm_plain``, ``tsmm_plain``), never a
+parity reference.
 
 Functions take host numpy arrays laid out exactly like the C-ABI's device
 buffers: row-major block vectors with leading dimensions in elements,
@@ -24,6 +27,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tsm_oracle.c")
+_SRC_PLAIN = os.path.join(_HERE, "tsm_plain.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
@@ -36,12 +40,12 @@ _OPS = {"T": OP_T, "C": OP_C, OP_T: OP_T, OP_C: OP_C}
 def build(force=False):
     """Compile the C oracle (plain -O2, no fast-math so rounding is IEEE)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_PLAIN))
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off",
-                           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+                           "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, _SRC_PLAIN, "-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -61,6 +65,12 @@ def _load():
             lib.oracle_tsmm.restype = ctypes.c_int
             lib.oracle_dot.argtypes = [ctypes.c_int, ctypes.c_int, i64, dp, dp, dp]
             lib.oracle_dot.restype = None
+            lib.oracle_tsmttsm_plain.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, i64,
+                                                 dp, dp, i64, dp, i64, dp, dp, i64, ctypes.c_int]
+            lib.oracle_tsmttsm_plain.restype = ctypes.c_int
+            lib.oracle_tsmm_plain.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64,
+                                              dp, dp, i64, dp, i64, dp, dp, i64, ctypes.c_int]
+            lib.oracle_tsmm_plain.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -99,6 +109,59 @@ def tsmttsm(op, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc):
     if rc:
         raise ValueError(f"oracle_tsmttsm rejected its arguments ({rc})")
     return C
+
+
+def tsmttsm_plain(op, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, threads=1):
+    """As ``tsmttsm`` but with the plain uncompensated sum of rounded
+    products, K cut into ``threads`` contiguous chunks summed in chunk
+    order: the CPU baseline that is timed, not a parity reference."""
+    cplx = np.iscomplexobj(A)
+    for arr, name in ((A, "A"), (B, "B"), (C, "C")):
+        _check(arr, cplx, name)
+    if A.size < K * lda or B.size < K * ldb or C.size < (M - 1) * ldc + N:
+        raise ValueError("buffer too small")
+    al, be = _scalar(alpha, cplx), _scalar(beta, cplx)
+    rc = _load().oracle_tsmttsm_plain(_OPS[op], int(cplx), M, N, K, _dptr(al), _dptr(A.view(np.float64)),
+                                      lda, _dptr(B.view(np.float64)), ldb, _dptr(be),
+                                      _dptr(C.view(np.float64)), ldc, int(threads))
+    if rc:
+        raise ValueError(f"oracle_tsmttsm_plain rejected its arguments ({rc})")
+    return C
+
+
+def gram_plain(A, B, op="T", threads=1):
+    """op(A)^T B by the plain threaded loop, for 2-D arrays."""
+    K, M = A.shape
+    N = B.shape[1]
+    C = np.zeros((M, N), dtype=A.dtype)
+    return tsmttsm_plain(op, M, N, K, 1.0, np.ascontiguousarray(A), M, np.ascontiguousarray(B), N, 0.0, C, N,
+                         threads)
+
+
+def tsmm_plain(M, N, K, alpha, A, lda, Cm, ldc, beta, B, ldb, threads=1):
+    """As ``tsmm`` with plain uncompensated row sums, rows split over
+    ``threads`` threads: the timed CPU baseline, not a parity reference."""
+    cplx = np.iscomplexobj(A)
+    for arr, name in ((A, "A"), (Cm, "C"), (B, "B")):
+        _check(arr, cplx, name)
+    if A.size < K * lda or B.size < K * ldb or Cm.size < (M - 1) * ldc + N:
+        raise ValueError("buffer too small")
+    al, be = _scalar(alpha, cplx), _scalar(beta, cplx)
+    rc = _load().oracle_tsmm_plain(int(cplx), M, N, K, _dptr(al), _dptr(A.view(np.float64)), lda,
+                                   _dptr(Cm.view(np.float64)), ldc, _dptr(be),
+                                   _dptr(B.view(np.float64)), ldb, int(threads))
+    if rc:
+        raise ValueError(f"oracle_tsmm_plain rejected its arguments ({rc})")
+    return B
+
+
+def apply_plain(A, Cm, alpha=1.0, beta=0.0, B0=None, threads=1):
+    """alpha * A C + beta * B0 by the plain threaded loop, for 2-D arrays."""
+    K, M = A.shape
+    N = Cm.shape[1]
+    B = np.zeros((K, N), dtype=A.dtype) if B0 is None else np.array(B0, dtype=A.dtype, order="C")
+    return tsmm_plain(M, N, K, alpha, np.ascontiguousarray(A), M, np.ascontiguousarray(Cm), N, beta, B, N,
+                      threads)
 
 
 def tsmm(M, N, K, alpha, A, lda, Cm, ldc, beta, B, ldb):
