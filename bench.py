@@ -1,28 +1,36 @@
 #!/usr/bin/env python
-"""Benchmark: TSMTTSM percent of roofline over the width sweep at K = 2^24.
+"""Benchmark: TSMTTSM / TSMM percent of roofline over the width sweeps at K = 2^24.
 
-One step = the whole sweep of plain-FP64 TSMTTSM calls (real with op T and
-complex with op C, alpha = 1, beta = 0) at K = 2^24 rows for
-M = N in {1, 2, 4, 8, 16, 32, 64} and (M, N) in {(1,64), (64,1), (8,32),
-(32,8)}: 22 kernel launches on inputs already resident in HBM.
+One step = one pass of both products over the width sweeps, on inputs
+already resident in HBM (58 kernel calls):
+  * TSMTTSM (real op T, complex op C; alpha = 1, beta = 0) for
+    M = N in {1, 2, 4, 8, 16, 32, 64} and (M, N) in {(1,64), (64,1), (8,32),
+    (32,8)};
+  * TSMM (alpha = 1, beta = 0 and beta = 1) for M = N in {1, ..., 64 by
+    powers of two} and (M, N) in {(4,64), (64,4)}.
 
 Roofline per call (Sec. 1.3, Eq. 1): flops = 2MNK (real) or 8MNK (complex),
-bytes = 8c(MK + NK + MN) (c = 2 for complex), P_max = min(I * b_s, P_fp64)
-with b_s the measured HBM bandwidth (MEASURED_PEAKS.json) and P_fp64 the
-larger of the nominal GB300 FP64 rate and the rate the DFMA probe measures
-live.  The reported value is whole-sweep efficiency:
-100 * sum(ideal time) / sum(measured time).
+bytes = 8c(MK + NK + MN) (c = 2 for complex; TSMM with beta != 0 also reads
+B: + 8cNK), P_max = min(I * b_s, P_fp64) with b_s the measured HBM copy
+bandwidth (MEASURED_PEAKS.json) and P_fp64 the FP64 rate measured live by
+the library's DFMA probe.  The reported value is whole-step efficiency:
+100 * sum(ideal time) / step time.
+
+Output: every extra measurement (per-width sweep, split path, small-K ramp,
+batched launch, cuBLAS, ...) is printed on a JSON line of its own
+({"extra": name, ...}) and, with --extras-out, written to one JSON file;
+the LAST stdout line is the compact headline record.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
        python bench.py --case c64:64x64 --k 1048576   (one kernel, for profiling)
 """
 
 import argparse
-import ctypes
 import hashlib
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -35,11 +43,17 @@ K_FULL = 1 << 24
 SQUARE = (1, 2, 4, 8, 16, 32, 64)
 OFFDIAG = ((1, 64), (64, 1), (8, 32), (32, 8))
 SWEEP = [(c, m, n) for c in (False, True) for (m, n) in [(w, w) for w in SQUARE] + list(OFFDIAG)]
-FP64_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 (vector and tensor), per GPU
+TSMM_SWEEP = [(c, m, n) for c in (False, True) for (m, n) in [(w, w) for w in SQUARE] + [(4, 64), (64, 4)]]
+# the calls of one step: (kind, complex, M, N, beta)
+STEP = [("tsmttsm", c, m, n, 0.0) for (c, m, n) in SWEEP] + \
+       [("tsmm", c, m, n, b) for (c, m, n) in TSMM_SWEEP for b in (0.0, 1.0)]
+FP64_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 (vector and tensor), per GPU, for context only
 HBM_FALLBACK_GBS = 6800.0
-WORKLOAD = ("TSMTTSM FP64 sweep, K=2^24, real (op T) + complex (op C), M=N in {1,2,4,8,16,32,64} "
-            "+ (M,N) in {(1,64),(64,1),(8,32),(32,8)}, alpha=1, beta=0, row-major, ld=width, "
-            "uniform(-1,1) SplitMix64 inputs (A seed 0, B seed 1)")
+METRIC = "TSMTTSM/TSMM % of roofline (HBM GB/s or FP64 TF/s) vs width 1–64, K=2^24"
+WORKLOAD = ("FP64 width sweeps at K=2^24, row-major, ld=width, uniform(-1,1) SplitMix64 inputs (A seed 0, "
+            "B seed 1, C seed 2): TSMTTSM real op T + complex op C, M=N in {1,2,4,...,64} + (M,N) in "
+            "{(1,64),(64,1),(8,32),(32,8)}, alpha=1, beta=0; TSMM real + complex, M=N in {1,2,4,...,64} + "
+            "(4,64),(64,4), alpha=1, beta in {0,1}")
 
 
 def model(cplx, M, N, K):
@@ -51,8 +65,18 @@ def model(cplx, M, N, K):
     return flops, nbytes
 
 
-def ideal_seconds(cplx, M, N, K, bw_gbs, p64_gflops):
+def call_model(kind, cplx, M, N, K, beta):
+    """(flops, bytes) of one call: Eq. 1, plus the read of B for a TSMM with
+    beta != 0 (and of C for a TSMTTSM with beta != 0)."""
     flops, nbytes = model(cplx, M, N, K)
+    c = 2 if cplx else 1
+    if beta != 0.0:
+        nbytes += 8.0 * c * (N * K if kind == "tsmm" else M * N)
+    return flops, nbytes
+
+
+def ideal_seconds(cplx, M, N, K, bw_gbs, p64_gflops, kind="tsmttsm", beta=0.0):
+    flops, nbytes = call_model(kind, cplx, M, N, K, beta)
     return max(nbytes / (bw_gbs * 1e9), flops / (p64_gflops * 1e9))
 
 
@@ -64,6 +88,32 @@ def load_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return HBM_FALLBACK_GBS, "fallback"
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
 # ------------------------------------------------------------------ clocks
@@ -132,11 +182,19 @@ class ClockSampler:
 
 def _kernel_source_hash(variant_name):
     """Hash of the sources that define a variant's kernel: the hand-written
-    FP64 family or the generator, plus their shared epilogue and header."""
+    FP64 family, the narrow kernels or the generator, plus their shared
+    epilogue and header."""
     h = hashlib.sha256()
     pkg = os.path.join(ROOT, "paper_1905_03136_gb300")
     files = ["csrc/fp64_common.cuh", "csrc/tsm_internal.h"]
-    files.append("codegen.py" if variant_name.startswith("gen_") else "csrc/kernels_fp64.cu")
+    if variant_name.startswith("gen_"):
+        files.append("codegen.py")
+    elif "narrow" in variant_name:
+        files.append("csrc/kernels_narrow.cu")
+    elif "_rt_" in variant_name:
+        files.append("csrc/kernels_rt.cu")
+    else:
+        files.append("csrc/kernels_fp64.cu")
     for name in files:
         with open(os.path.join(pkg, name), "rb") as f:
             h.update(f.read())
@@ -169,52 +227,101 @@ def _views(flatA, flatB, cplx, M, N, K):
     return a.view(K, M), b.view(K, N)
 
 
-def cpu_oracle_sweep(K_sample, K_full, bw, p64):
-    """Times the CPU oracle (single thread, as it stands) on the first
-    K_sample rows of every sweep configuration; returns (value, seconds,
-    per-config list) with times scaled linearly to K_full rows."""
+def _mat(flat, rows, cols, cplx):
+    """A (rows x cols) row-major view of the start of a flat float64 buffer."""
+    import torch
+    v = flat[: rows * cols * (2 if cplx else 1)]
+    if cplx:
+        v = v.view(torch.complex128)
+    return v.view(rows, cols)
+
+
+# ------------------------------------------------------------------ CPU baseline
+
+def _host_flat(seed, rows):
+    """Flat host buffer of rows x 128 doubles: by the element addressing of
+    ``synth`` its first K*w(*2) doubles are the seeded input of every width
+    w (and of every complex width) with ld = w."""
+    import synth
+    return synth.block_vector(seed, rows, 128).reshape(-1)
+
+
+def cpu_step(hA, hB, hC, hO, K, threads):
+    """Seconds of one step of the plain CPU loops on the first K rows of every
+    call of the step (input generation outside the timed region)."""
     import numpy as np
     import oracle
-    import synth
-    total_ideal = 0.0
-    total_cpu = 0.0
-    wall = 0.0
-    for (cplx, M, N) in SWEEP:
-        A = synth.block_vector(synth.SEED_A, K_sample, M, complex_=cplx)
-        B = synth.block_vector(synth.SEED_B, K_sample, N, complex_=cplx)
-        C = np.zeros((M, N), dtype=A.dtype)
-        t0 = time.perf_counter()
-        oracle.tsmttsm("C" if cplx else "T", M, N, K_sample, 1.0, A, M, B, N, 0.0, C, N)
-        dt = time.perf_counter() - t0
-        wall += dt
-        total_cpu += dt * K_full / K_sample
-        total_ideal += ideal_seconds(cplx, M, N, K_full, bw, p64)
-    return 100.0 * total_ideal / total_cpu, wall
+    secs = []
+    for (kind, cplx, M, N, beta) in STEP:
+        dt = np.complex128 if cplx else np.float64
+        c = 2 if cplx else 1
+        A = hA[: K * M * c].view(dt)
+        if kind == "tsmttsm":
+            B = hB[: K * N * c].view(dt)
+            C = np.zeros(M * N, dtype=dt)
+            t0 = time.perf_counter()
+            oracle.tsmttsm_plain("C" if cplx else "T", M, N, K, 1.0, A, M, B, N, 0.0, C, N, threads)
+        else:
+            Cm = hC[: M * N * c].view(dt)
+            O = hO[: K * N * c].view(dt)
+            t0 = time.perf_counter()
+            oracle.tsmm_plain(M, N, K, 1.0, A, M, Cm, N, beta, O, N, threads)
+        secs.append(time.perf_counter() - t0)
+    return secs
+
+
+def cpu_baseline(K_single, K_all, bw, p64):
+    """The plain CPU loops (oracle/tsm_plain.c, as they stand) on one host
+    core and on every host core, each on the first rows of every call of
+    the step, times scaled linearly to K = 2^24 (every call's work grows
+    linearly in K).  Returns the cpu_baseline record."""
+    import numpy as np
+    Kmax = max(K_single, K_all)
+    hA, hB = _host_flat(0, Kmax), _host_flat(1, Kmax)
+    hC = _host_flat(2, 64)
+    hO = np.zeros(Kmax * 128)
+    ideal = sum(ideal_seconds(c, M, N, K_FULL, bw, p64, kind, b) for (kind, c, M, N, b) in STEP)
+    cores = host_cores()
+    out = {}
+    for label, K, T in (("single", K_single, 1), ("all", K_all, cores)):
+        secs = cpu_step(hA, hB, hC, hO, K, T)
+        out[label] = (100.0 * ideal / (sum(secs) * K_FULL / K), sum(secs))
+    return {"value": out["all"][0], "unit": "% of roofline", "cores": cores, "kind": "oracle",
+            "sample": "plain uncompensated loops of oracle/tsm_plain.c: first %d rows of each of the %d calls "
+                      "on %d threads (%.1f s), first %d rows on 1 thread (%.1f s); times scaled to 2^24 rows"
+                      % (K_all, len(STEP), cores, out["all"][1], K_single, out["single"][1]),
+            "single_core_value": out["single"][0], "cpu": cpu_model()}
 
 
 # ------------------------------------------------------------------ arms
 
 def run_reference(args, bw, bw_src):
-    """The oracle as the reference arm: each step a bounded sample of the
-    sweep on the host (single-threaded C oracle)."""
+    """The reference arm: the plain CPU loops on every host core, each step a
+    bounded sample (the first --ref-rows rows of every call of the step,
+    times scaled linearly to 2^24 rows)."""
+    import numpy as np
     p64 = FP64_NOMINAL_GFLOPS
     K_s = args.ref_rows
+    hA, hB, hC = _host_flat(0, K_s), _host_flat(1, K_s), _host_flat(2, 64)
+    hO = np.zeros(K_s * 128)
+    cores = host_cores()
+    ideal = sum(ideal_seconds(c, M, N, K_FULL, bw, p64, kind, b) for (kind, c, M, N, b) in STEP)
     for _ in range(args.warmup):
-        cpu_oracle_sweep(K_s, K_FULL, bw, p64)
-    vals, walls = [], []
+        cpu_step(hA, hB, hC, hO, K_s, cores)
+    walls = []
     for _ in range(args.steps):
-        v, w = cpu_oracle_sweep(K_s, K_FULL, bw, p64)
-        vals.append(v)
-        walls.append(w)
-    value = statistics.mean(vals)
-    sample = "first %d of 2^24 rows of each of the 22 sweep configurations, times scaled x%d" % (K_s, K_FULL // K_s)
-    line = {"impl": "reference", "metric": "TSMTTSM % of roofline vs width, K=2^24", "value": value,
+        walls.append(sum(cpu_step(hA, hB, hC, hO, K_s, cores)))
+    secs = statistics.mean(walls)
+    value = 100.0 * ideal / (secs * K_FULL / K_s)
+    sample = ("plain uncompensated loops of oracle/tsm_plain.c on %d threads: first %d of 2^24 rows of each of "
+              "the %d calls of the step, times scaled x%d" % (cores, K_s, len(STEP), K_FULL // K_s))
+    line = {"impl": "reference", "metric": METRIC, "value": value,
             "unit": "% of roofline", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * statistics.mean(walls), "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * secs, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (SplitMix64 seeded)",
             "config": {"workload": WORKLOAD, "K": K_FULL, "parallelism": "replicas"},
-            "cpu_baseline": {"value": value, "unit": "% of roofline", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "% of roofline", "cores": cores, "kind": "oracle",
+                             "sample": sample, "cpu": cpu_model()},
             "e2e": {"value": value, "unit": "% of roofline", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "peaks": {"hbm_gbs": bw, "hbm_source": bw_src, "fp64_gflops": p64, "fp64_source": "nominal"}}
     print(json.dumps(line), flush=True)
@@ -231,17 +338,24 @@ def run_case(args):
     c = 2 if cplx else 1
     K = args.k
     fa = torch.empty(K * M * c, dtype=torch.float64, device="cuda")
-    fb = torch.empty(K * N * c, dtype=torch.float64, device="cuda")
+    fb = torch.empty(K * max(M, N) * c, dtype=torch.float64, device="cuda")
     tsm.fill_random(fa.view(1, -1), 0)
     tsm.fill_random(fb.view(1, -1), 1)
-    A, B = _views(fa, fb, cplx, M, N, K)
-    C = torch.zeros((M, N), dtype=A.dtype, device="cuda")
-    for _ in range(args.steps):
-        if args.split:
-            from paper_1905_03136_gb300 import split
-            split.tsmttsm_split(A, B, C, op="C" if cplx else "T")
-        else:
-            tsm.tsmttsm(A, B, C, op="C" if cplx else "T")
+    if args.tsmm:
+        A = _mat(fa, K, M, cplx)
+        Cm = _mat(fb, M, N, cplx).clone()
+        Bo = _mat(fb, K, N, cplx)
+        for _ in range(args.steps):
+            tsm.tsmm(A, Cm, Bo, 1.0, args.beta)
+    else:
+        A, B = _views(fa, fb, cplx, M, N, K)
+        C = torch.zeros((M, N), dtype=A.dtype, device="cuda")
+        for _ in range(args.steps):
+            if args.split:
+                from paper_1905_03136_gb300 import split
+                split.tsmttsm_split(A, B, C, op="C" if cplx else "T")
+            else:
+                tsm.tsmttsm(A, B, C, op="C" if cplx else "T")
     torch.cuda.synchronize()
     print(json.dumps({"case": args.case, "K": K, "ok": True}))
 
@@ -258,6 +372,22 @@ def max_over_ranks(x, device=None):
     return float(t.item())
 
 
+def measure_fp64_peak(local):
+    """The FP64 rate of the library's probes (DFMA register tile, FP64 MMA,
+    constant-operand DFMA chain), with the SM clock sampled while they run.
+    The register-tile DFMA form is the one the products use."""
+    from paper_1905_03136_gb300 import probe
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.2)
+    dfma = probe.fp64_peak(0, iters=40000)
+    dmma = probe.fp64_peak(1, iters=20000)
+    chain = probe.fp64_peak(2, iters=40000)
+    info = clocks.stop()
+    return {"dfma_tile": dfma, "dmma": dmma, "dfma_chain": chain, "sm_mhz": info.get("sm_mhz"),
+            "reasons": info.get("reasons")}
+
+
 def run_ours(args, bw, bw_src):
     import torch
     import torch.distributed as dist
@@ -270,45 +400,68 @@ def run_ours(args, bw, bw_src):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     import paper_1905_03136_gb300 as tsm
-    from paper_1905_03136_gb300 import probe
-    tsm.load()
+    lib = tsm.load()
     dev = torch.device("cuda", local)
     K = K_FULL
+    extras_file = {}
 
-    # Inputs: one flat buffer per operand, seeded once (outside timing).
+    def emit(name, rec):
+        """An extra measurement: its own stdout line now, the file later."""
+        extras_file[name] = rec
+        if rank == 0:
+            print(json.dumps({"extra": name, **(rec if isinstance(rec, dict) else {"value": rec})}), flush=True)
+
+    # Inputs: one flat buffer per operand, seeded once (outside timing).  By
+    # the generator's element addressing the prefix of K*w(*2) doubles is the
+    # seeded input of every width w with ld = w (see _host_flat).
     flatA = torch.empty(K * 128, dtype=torch.float64, device=dev)
     flatB = torch.empty(K * 128, dtype=torch.float64, device=dev)
+    flatC = torch.empty(64 * 128, dtype=torch.float64, device=dev)
+    Bout = torch.zeros(K * 128, dtype=torch.float64, device=dev)
     tsm.fill_random(flatA.view(K, 128), 0)
     tsm.fill_random(flatB.view(K, 128), 1)
-    outs = {cfg: torch.zeros((cfg[1], cfg[2]), dtype=torch.complex128 if cfg[0] else torch.float64, device=dev)
-            for cfg in SWEEP}
-    views = {cfg: _views(flatA, flatB, cfg[0], cfg[1], cfg[2], K) for cfg in SWEEP}
-    chosen = {cfg: tsm.choose(tsm.KIND_TSMTTSM, tsm.C64 if cfg[0] else tsm.R64, cfg[1], cfg[2], K) for cfg in SWEEP}
-    names = {v["index"]: v["name"] for v in tsm.variants(tsm.KIND_TSMTTSM)}
+    tsm.fill_random(flatC.view(64, 128), 2)
+    kdt = {False: tsm.R64, True: tsm.C64}
 
-    dfma = probe.fp64_peak(0)
-    dmma = probe.fp64_peak(1)
-    p64 = max(FP64_NOMINAL_GFLOPS, dfma, dmma)
-    p64_src = "nominal" if p64 == FP64_NOMINAL_GFLOPS else ("measured DFMA probe" if p64 == dfma else
-                                                             "measured DMMA probe")
+    calls = []
+    for (kind, cplx, M, N, beta) in STEP:
+        A = _mat(flatA, K, M, cplx)
+        if kind == "tsmttsm":
+            B = _mat(flatB, K, N, cplx)
+            out = torch.zeros((M, N), dtype=A.dtype, device=dev)
+            var, grid = tsm.choose(tsm.KIND_TSMTTSM, kdt[cplx], M, N, K)
+            fn = (lambda A=A, B=B, out=out, op=("C" if cplx else "T"): tsm.tsmttsm(A, B, out, op=op))
+            launches = lib.tsm_tsmttsm_kernels_per_call(kdt[cplx], M, N, grid)
+        else:
+            Cm = _mat(flatC, M, N, cplx)
+            out = _mat(Bout, K, N, cplx)
+            var, grid = tsm.choose(tsm.KIND_TSMM_BETA if beta else tsm.KIND_TSMM, kdt[cplx], M, N, K)
+            fn = (lambda A=A, Cm=Cm, out=out, beta=beta: tsm.tsmm(A, Cm, out, 1.0, beta))
+            launches = 1
+        calls.append({"key": (kind, cplx, M, N, beta), "fn": fn, "var": var, "grid": grid, "launches": launches})
+    names = {k: {v["index"]: v["name"] for v in tsm.variants(k)} for k in (tsm.KIND_TSMTTSM, tsm.KIND_TSMM)}
+
+    fp64 = measure_fp64_peak(local)
+    p64 = max(fp64["dfma_tile"], fp64["dmma"], fp64["dfma_chain"])
+    p64_src = "measured: DFMA register-tile probe at %s MHz" % fp64["sm_mhz"] if p64 == fp64["dfma_tile"] else \
+        "measured: %s probe" % ("FP64 MMA" if p64 == fp64["dmma"] else "DFMA chain")
 
     stream = torch.cuda.current_stream()
 
     def step(record=None):
-        for cfg in SWEEP:
-            A, B = views[cfg]
+        for i, cl in enumerate(calls):
             if record is not None:
-                record[cfg][0].record(stream)
-            tsm.tsmttsm(A, B, outs[cfg], op="C" if cfg[0] else "T")
+                record[i][0].record(stream)
+            cl["fn"]()
             if record is not None:
-                record[cfg][1].record(stream)
+                record[i][1].record(stream)
 
     for _ in range(max(args.warmup, 0)):
         step()
     torch.cuda.synchronize()
 
-    events = [{cfg: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for cfg in SWEEP} for _ in range(args.steps)]
+    events = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in calls]
+              for _ in range(args.steps)]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
     if world > 1:
@@ -327,157 +480,179 @@ def run_ours(args, bw, bw_src):
     total_ms = t_start.elapsed_time(t_end)
     # Per-call times are medians over the steps: the first call of the first
     # timed step starts on an idle GPU and so also holds the host's launch
-    # latency (the whole-step value above keeps it).
-    per_cfg = {cfg: statistics.median(events[s][cfg][0].elapsed_time(events[s][cfg][1])
-                                      for s in range(args.steps))
-               for cfg in SWEEP}
+    # latency (the whole-step value keeps it).
+    per_call = [statistics.median(events[s][i][0].elapsed_time(events[s][i][1]) for s in range(args.steps))
+                for i in range(len(calls))]
 
-    ideal = {cfg: ideal_seconds(cfg[0], cfg[1], cfg[2], K, bw, p64) for cfg in SWEEP}
+    ideal = [ideal_seconds(cplx, M, N, K, bw, p64, kind, beta) for (kind, cplx, M, N, beta) in STEP]
     ms_step = max_over_ranks(total_ms / args.steps, dev)
-    value = 100.0 * sum(ideal.values()) / (ms_step * 1e-3)
+    value = 100.0 * sum(ideal) / (ms_step * 1e-3)
 
-    sweep = []
-    for cfg in SWEEP:
-        flops, nbytes = model(cfg[0], cfg[1], cfg[2], K)
-        ms = per_cfg[cfg]
-        bound = "fp64" if flops / (p64 * 1e9) >= nbytes / (bw * 1e9) else "hbm"
-        sweep.append({"dtype": "c64" if cfg[0] else "r64", "M": cfg[1], "N": cfg[2], "ms": round(ms, 4),
-                      "gflops": round(flops / (ms * 1e-3) / 1e9, 2), "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
-                      "roofline_pct": round(100.0 * ideal[cfg] / (ms * 1e-3), 2), "bound": bound,
-                      "variant": names[chosen[cfg][0]], "grid": chosen[cfg][1]})
+    rows = []
+    for i, cl in enumerate(calls):
+        kind, cplx, M, N, beta = cl["key"]
+        flops, nbytes = call_model(kind, cplx, M, N, K, beta)
+        ms = per_call[i]
+        nm = names[tsm.KIND_TSMTTSM if kind == "tsmttsm" else tsm.KIND_TSMM][cl["var"]]
+        rows.append({"kind": kind, "dtype": "c64" if cplx else "r64", "M": M, "N": N, "beta": beta,
+                     "ms": round(ms, 4), "gflops": round(flops / (ms * 1e-3) / 1e9, 2),
+                     "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                     "roofline_pct": round(100.0 * ideal[i] / (ms * 1e-3), 2),
+                     "bound": "fp64" if flops / (p64 * 1e9) >= nbytes / (bw * 1e9) else "hbm",
+                     "variant": nm, "grid": cl["grid"]})
+    emit("step_calls", {"calls": rows})
+    part = {}
+    for kind in ("tsmttsm", "tsmm"):
+        idx = [i for i, cl in enumerate(calls) if cl["key"][0] == kind]
+        part[kind] = round(100.0 * sum(ideal[i] for i in idx) / (1e-3 * sum(per_call[i] for i in idx)), 2)
 
-    # our kernels per step: one per call, plus the final reduction pass of
-    # the calls with many CTA partials
-    lib = tsm.load()
-    launches_per_step = sum(lib.tsm_tsmttsm_kernels_per_call(tsm.C64 if c[0] else tsm.R64, c[1], c[2],
-                                                             chosen[c][1]) for c in SWEEP)
+    launches_per_step = sum(cl["launches"] for cl in calls)
 
     # Dominant kernel: the longest call of the step.
-    dom = max(SWEEP, key=lambda c: per_cfg[c])
-    flops, nbytes = model(dom[0], dom[1], dom[2], K)
-    dom_ms = per_cfg[dom]
-    fp64_bound = flops / (p64 * 1e9) >= nbytes / (bw * 1e9)
-    if fp64_bound:
+    d = max(range(len(calls)), key=lambda i: per_call[i])
+    kind, cplx, M, N, beta = calls[d]["key"]
+    flops, nbytes = call_model(kind, cplx, M, N, K, beta)
+    dom_ms = per_call[d]
+    dom_name = names[tsm.KIND_TSMTTSM if kind == "tsmttsm" else tsm.KIND_TSMM][calls[d]["var"]]
+    if flops / (p64 * 1e9) >= nbytes / (bw * 1e9):
         achieved = flops / (dom_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": p64 / 1e3, "unit": "TFLOP/s",
-                "frac": achieved / (p64 / 1e3), "peak_source": "FP64 pipe, " + p64_src}
+        roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(p64 / 1e3, 4), "unit": "TFLOP/s",
+                "frac": round(achieved / (p64 / 1e3), 4), "peak_source": "FP64 pipe, " + p64_src}
     else:
         achieved = nbytes / (dom_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": bw, "unit": "GB/s", "frac": achieved / bw,
-                "peak_source": bw_src}
-    cfg_key = "%s:%dx%d" % ("c64" if dom[0] else "r64", dom[1], dom[2])
-    roof["traffic"] = _traffic_for(names[chosen[dom][0]], cfg_key)
-    roof["kernel"] = names[chosen[dom][0]]
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": bw, "unit": "GB/s",
+                "frac": round(achieved / bw, 4), "peak_source": bw_src}
+    cfg_key = "%s:%s:%dx%d%s" % (kind, "c64" if cplx else "r64", M, N, ":beta1" if beta else "")
+    roof["traffic"] = _traffic_for(dom_name, cfg_key)
+    roof["kernel"] = dom_name
     roof["config"] = cfg_key
+    roof["ms"] = round(dom_ms, 3)
 
-    # End to end: host (pinned) inputs copied in and C copied out every call.
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, flatA, flatB, outs, views, ideal, dev, K)
+        e2e = run_e2e(calls, flatA, flatB, flatC, sum(ideal), dev, K)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, wall = cpu_oracle_sweep(args.cpu_rows, K, bw, p64)
-        cpu = {"value": v, "unit": "% of roofline", "cores": 1, "kind": "oracle",
-               "sample": "first %d of 2^24 rows of each of the 22 sweep configurations (%.1f s of CPU), "
-                         "times scaled x%d" % (args.cpu_rows, wall, K // args.cpu_rows)}
+        cpu = cpu_baseline(args.cpu_rows, args.cpu_rows_all, bw, p64)
 
-    extras = {}
+    summary = {}
     if rank == 0 and not args.no_extras:
-        extras = run_extras(args, flatA, flatB, K, bw, p64)
+        summary = run_extras(args, flatA, flatB, K, bw, p64, emit)
 
     if rank == 0:
-        line = {"metric": "TSMTTSM % of roofline vs width, K=2^24", "value": value, "unit": "% of roofline",
-                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        emit("peaks", {"hbm_gbs": bw, "hbm_source": bw_src, "fp64_gflops_used": p64, "fp64_source": p64_src,
+                       "fp64_nominal_gflops": FP64_NOMINAL_GFLOPS, "probes": fp64})
+        if args.extras_out:
+            with open(args.extras_out, "w") as f:
+                json.dump(extras_file, f)
+        line = {"metric": METRIC, "value": round(value, 3), "unit": "% of roofline",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic (SplitMix64 seeded, generated on device)",
-                "config": {"workload": WORKLOAD, "K": K, "calls_per_step": len(SWEEP),
-                           "l2": "inputs 2^24 rows >> 129 MB L2 except the C outputs; no flush",
+                "config": {"workload": "TSMTTSM 22-call + TSMM 36-call FP64 width sweeps, K=2^24 (A seed 0, "
+                                       "B seed 1, C seed 2, uniform(-1,1))", "K": K, "calls_per_step": len(calls),
+                           "l2": "inputs 2^24 rows >> 129 MB L2; no flush",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "gpu_launches": launches_per_step * args.steps,
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clock_info,
-                "peaks": {"hbm_gbs": bw, "hbm_source": bw_src, "fp64_gflops_used": p64,
-                          "fp64_source": p64_src, "fp64_nominal_gflops": FP64_NOMINAL_GFLOPS,
-                          "dfma_probe_gflops": dfma, "dmma_probe_gflops": dmma},
-                "sweep": sweep}
-        line.update(extras)
-        print(json.dumps(line), flush=True)
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": {k: clock_info.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons", "power_w_max")},
+                "fp64_peak_gflops": round(p64, 1),
+                "by_product_pct": part}
+        line.update(summary)
+        text = json.dumps(line)
+        if len(text) > 2600:  # the headline must stay short: drop the extras summary first
+            for k in list(summary):
+                line.pop(k, None)
+            text = json.dumps(line)
+        print(text, flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
 
 
-def run_e2e(args, flatA, flatB, outs, views, ideal, dev, K):
-    """One sweep where every call's A and B come from pinned host memory and
-    the C results go back to the host: the same metric measured end to end.
-    Each configuration's inputs are copied in full (no reuse across calls);
-    the copies of the next configurations overlap the current kernel through
-    a second stream and four device slots, and the 22 small results are read
-    back behind the last product (a read-back after every call, on the
-    compute stream, stalled the pipeline: one sweep took 2.7 s instead of
-    1.4 s)."""
+def run_e2e(calls, flatA, flatB, flatC, ideal_s, dev, K):
+    """One step of the same 58 calls through the public API with host
+    inputs: every call's A, B and C come from pinned host memory and every
+    result goes back to pinned host memory, copies inside the timed region.
+    Copies of the next calls run on a copy-in stream up to two calls ahead
+    of the products (three device slots); TSMM results go back on a
+    copy-out stream as soon as their kernel ends; the 22 small TSMTTSM
+    results are read back behind the last product."""
     import torch
+    import paper_1905_03136_gb300 as tsm
     try:
         hA = torch.empty(flatA.numel(), dtype=torch.float64, pin_memory=True)
         hB = torch.empty(flatB.numel(), dtype=torch.float64, pin_memory=True)
+        hO = torch.empty(flatB.numel(), dtype=torch.float64, pin_memory=True)
         pinned = True
     except Exception:
         hA = torch.empty(flatA.numel(), dtype=torch.float64)
         hB = torch.empty(flatB.numel(), dtype=torch.float64)
+        hO = torch.empty(flatB.numel(), dtype=torch.float64)
         pinned = False
     hA.copy_(flatA)
     hB.copy_(flatB)
-    nslot = 4  # device slots: the copies may run three calls ahead of the products
-    slots = [(torch.empty_like(flatA), torch.empty_like(flatB)) for _ in range(nslot)]
-    hC = {cfg: torch.empty(outs[cfg].shape, dtype=outs[cfg].dtype, pin_memory=pinned) for cfg in SWEEP}
-    import paper_1905_03136_gb300 as tsm
+    hCin = flatC.cpu()
+    nslot = 3
+    slots = [(torch.empty_like(flatA), torch.empty_like(flatB), torch.empty_like(flatC)) for _ in range(nslot)]
+    small_out = []
     compute = torch.cuda.current_stream()
-    copier = torch.cuda.Stream()
+    cin, cout = torch.cuda.Stream(), torch.cuda.Stream()
+    n = len(calls)
+    copied = [torch.cuda.Event() for _ in range(n)]
+    done = [torch.cuda.Event() for _ in range(n)]
+    freed = [torch.cuda.Event() for _ in range(n)]
     h2d = d2h = 0
-    copied = [torch.cuda.Event() for _ in SWEEP]
-    done = [torch.cuda.Event() for _ in SWEEP]
     torch.cuda.synchronize()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record(compute)
-    copier.wait_event(t0)
-    for i, cfg in enumerate(SWEEP):
-        cplx, M, N = cfg
+    cin.wait_event(t0)
+    for i, cl in enumerate(calls):
+        kind, cplx, M, N, beta = cl["key"]
         c = 2 if cplx else 1
+        dA, dB, dC = slots[i % nslot]
         na, nb = K * M * c, K * N * c
-        dA, dB = slots[i % nslot]
-        with torch.cuda.stream(copier):
+        with torch.cuda.stream(cin):
             if i >= nslot:
-                copier.wait_event(done[i - nslot])
+                cin.wait_event(freed[i - nslot])
             dA[:na].copy_(hA[:na], non_blocking=True)
-            dB[:nb].copy_(hB[:nb], non_blocking=True)
-            copied[i].record(copier)
+            h2d += 8 * na
+            if kind == "tsmttsm" or beta != 0.0:
+                dB[:nb].copy_(hB[:nb], non_blocking=True)
+                h2d += 8 * nb
+            if kind == "tsmm":
+                dC[: M * N * c].copy_(hCin[: M * N * c], non_blocking=True)
+                h2d += 8 * M * N * c
+            copied[i].record(cin)
         compute.wait_event(copied[i])
-        A, B = _views(dA, dB, cplx, M, N, K)
-        tsm.tsmttsm(A, B, outs[cfg], op="C" if cplx else "T")
-        done[i].record(compute)
-        h2d += 8 * (na + nb)
-    # the step's results back to the host, behind the last product
-    for cfg in SWEEP:
-        hC[cfg].copy_(outs[cfg], non_blocking=True)
-        d2h += outs[cfg].numel() * outs[cfg].element_size()
+        A = _mat(dA, K, M, cplx)
+        if kind == "tsmttsm":
+            out = torch.empty((M, N), dtype=A.dtype, device=dev)
+            tsm.tsmttsm(A, _mat(dB, K, N, cplx), out, op="C" if cplx else "T")
+            small_out.append(out)
+            done[i].record(compute)
+            freed[i] = done[i]
+        else:
+            tsm.tsmm(A, _mat(dC, M, N, cplx), _mat(dB, K, N, cplx), 1.0, beta)
+            done[i].record(compute)
+            with torch.cuda.stream(cout):
+                cout.wait_event(done[i])
+                hO[:nb].copy_(dB[:nb], non_blocking=True)
+                d2h += 8 * nb
+                freed[i].record(cout)
+    hsmall = [torch.empty(o.shape, dtype=o.dtype, pin_memory=pinned) for o in small_out]
+    for h, o in zip(hsmall, small_out):
+        h.copy_(o, non_blocking=True)
+        d2h += o.numel() * o.element_size()
+    compute.wait_stream(cout)
     t1.record(compute)
     torch.cuda.synchronize()
     secs = t0.elapsed_time(t1) * 1e-3
-    # raw pinned host-to-device bandwidth of one large copy, for context
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(compute)
-    slots[0][0].copy_(hA, non_blocking=True)
-    e1.record(compute)
-    torch.cuda.synchronize()
-    h2d_gbs = 8.0 * hA.numel() / (e0.elapsed_time(e1) * 1e-3) / 1e9
-    del slots, hA, hB
+    del slots, hA, hB, hO
     torch.cuda.empty_cache()
-    return {"value": 100.0 * sum(ideal.values()) / secs, "unit": "% of roofline", "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "ms_per_step": secs * 1e3, "pinned": pinned,
-            "h2d_gbs_single_copy": round(h2d_gbs, 1),
-            "note": "every call copies its own A and B (no reuse) on a copy stream running up to three calls "
-                    "ahead of the products (four device slots); the C results are read back at the end of the step"}
+    return {"value": round(100.0 * ideal_s / secs, 3), "unit": "% of roofline", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": round(secs * 1e3, 1), "pinned": pinned}
 
 
 # ------------------------------------------------------------------ extras
@@ -508,13 +683,28 @@ def _time(fn, reps=3, warm=1):
 
 
 SPLIT_CASES = [(True, 32, 32), (True, 48, 48), (True, 64, 64), (False, 64, 64)]
-TSMM_SWEEP = [(c, m, n) for c in (False, True) for (m, n) in [(w, w) for w in SQUARE] + [(4, 64), (64, 4)]]
+
+
+def _oracle_entries(cplx, M, N, K, dist, entries):
+    """Entries (m, n) of op(A)^T B at full K computed by the oracle from the
+    host generator's columns (never from the device), with the
+    Cauchy-Schwarz scale ||a_m|| ||b_n|| of each."""
+    import numpy as np
+    import oracle
+    import synth
+    out = []
+    for (m, n) in entries:
+        a = synth.column(0, K, m, M, complex_=cplx, dist=dist)
+        b = synth.column(1, K, n, N, complex_=cplx, dist=dist)
+        out.append((oracle.dot("C" if cplx else "T", a, b), float(np.linalg.norm(a) * np.linalg.norm(b))))
+    return out
 
 
 def run_split_extra(flatA, flatB, K, bw):
     """Split-precision TSMTTSM on the split workload: time, speed-up over the
-    plain FP64 path, HBM fraction, and its normwise difference from the FP64
-    path's result (both on the GPU; the oracle pins both in the tests)."""
+    plain FP64 path, HBM fraction, and the error of two sampled entries
+    ((0, 0) and (M-1, N-1)) against the oracle's values at full K, relative
+    to each entry and to its Cauchy-Schwarz scale ||a_m|| ||b_n||."""
     import torch
     import paper_1905_03136_gb300 as tsm
     from paper_1905_03136_gb300 import split
@@ -530,42 +720,23 @@ def run_split_extra(flatA, flatB, K, bw):
             ms_s = _time(lambda: split.tsmttsm_split(A, B, C1, op=op))
             status = split.status()
             ms_d = _time(lambda: tsm.tsmttsm(A, B, C2, op=op), reps=1)
-            rel = float(torch.linalg.norm(C1 - C2) / torch.linalg.norm(C2))
+            h1 = C1.cpu().numpy()
+            ents = [(0, 0), (M - 1, N - 1)]
+            ref = _oracle_entries(cplx, M, N, K, dist, ents)
+            err_rel = max(abs(h1[m, n] - r) / abs(r) for (m, n), (r, _) in zip(ents, ref))
+            err_cs = max(abs(h1[m, n] - r) / s for (m, n), (r, s) in zip(ents, ref))
             c = 2 if cplx else 1
             nbytes = 8.0 * c * (M + N) * K
             out.append({"dist": dist, "dtype": "c64" if cplx else "r64", "M": M, "N": N,
                         "ms_split": round(ms_s, 3), "ms_fp64": round(ms_d, 3), "speedup": round(ms_d / ms_s, 2),
                         "split_gbs": round(nbytes / (ms_s * 1e-3) / 1e9, 1),
                         "hbm_frac": round(nbytes / (ms_s * 1e-3) / 1e9 / bw, 3),
-                        "rel_diff_vs_fp64_path": rel, "status": status})
+                        "oracle_entry_rel_err": err_rel, "oracle_entry_err_vs_norms": err_cs,
+                        "rel_diff_vs_fp64_path": float(torch.linalg.norm(C1 - C2) / torch.linalg.norm(C2)),
+                        "status": status})
     tsm.fill_random(flatA.view(K, 128), 0)
     tsm.fill_random(flatB.view(K, 128), 1)
     return out
-
-
-def run_tsmm_extra(flatA, flatB, K, bw, p64):
-    import torch
-    import paper_1905_03136_gb300 as tsm
-    out, ideal, meas = [], 0.0, 0.0
-    Bout = torch.empty(K * 128, dtype=torch.float64, device=flatA.device)
-    for (cplx, M, N) in TSMM_SWEEP:
-        c = 2 if cplx else 1
-        A = flatA[: K * M * c]
-        Cm = flatB[: M * N * c]
-        Bo = Bout[: K * N * c]
-        if cplx:
-            A, Cm, Bo = A.view(torch.complex128), Cm.view(torch.complex128), Bo.view(torch.complex128)
-        A, Cm, Bo = A.view(K, M), Cm.view(M, N), Bo.view(K, N)
-        flops, nbytes = model(cplx, M, N, K)
-        t_ideal = max(nbytes / (bw * 1e9), flops / (p64 * 1e9))
-        ms = _time(lambda: tsm.tsmm(A, Cm, Bo), reps=_reps_for(t_ideal))
-        ideal += t_ideal
-        meas += ms * 1e-3
-        out.append({"dtype": "c64" if cplx else "r64", "M": M, "N": N, "ms": round(ms, 4),
-                    "roofline_pct": round(100 * t_ideal / (ms * 1e-3), 2)})
-    del Bout
-    torch.cuda.empty_cache()
-    return {"roofline_pct_whole_sweep": 100 * ideal / meas, "calls": out}
 
 
 def run_widths_extra(flatA, flatB, K, bw, p64):
@@ -832,53 +1003,62 @@ def run_cublas_extra(flatA, flatB, K, bw, p64):
             "value": 100.0 * ideal_sum / meas_sum, "unit": "% of roofline", "sweep": rows}
 
 
-def run_extras(args, flatA, flatB, K, bw, p64):
-    ex = {}
-    try:
-        ex["cublas"] = run_cublas_extra(flatA, flatB, K, bw, p64)
-    except Exception as e:  # reported, never hidden
-        ex["cublas"] = {"error": repr(e)}
-    try:
-        ex["split"] = run_split_extra(flatA, flatB, K, bw)
-    except Exception as e:  # reported, never hidden
-        ex["split"] = {"error": repr(e)}
-    try:
-        ex["tsmm_sweep"] = run_tsmm_extra(flatA, flatB, K, bw, p64)
-    except Exception as e:
-        ex["tsmm_sweep"] = {"error": repr(e)}
-    try:
-        ex["widths"] = run_widths_extra(flatA, flatB, K, bw, p64)
-    except Exception as e:
-        ex["widths"] = {"error": repr(e)}
-    try:
-        ex["gs_step"] = run_gs_extra(flatA, flatB, K, bw, p64)
-    except Exception as e:
-        ex["gs_step"] = {"error": repr(e)}
-    try:
-        ex["small_k_ramp"] = run_ramp_extra(flatA, flatB, bw, p64)
-    except Exception as e:
-        ex["small_k_ramp"] = {"error": repr(e)}
-    try:
-        ex["batched"] = run_batched_extra(flatA, flatB)
-    except Exception as e:
-        ex["batched"] = {"error": repr(e)}
-    return ex
+def run_extras(args, flatA, flatB, K, bw, p64, emit):
+    """Runs every extra, emits each one, and returns the short summary the
+    headline line carries."""
+    summ = {}
+
+    def guarded(name, fn):
+        try:
+            rec = fn()
+        except Exception as e:  # reported, never hidden
+            rec = {"error": repr(e)}
+        emit(name, rec if isinstance(rec, dict) else {"rows": rec})
+        return rec
+
+    w = guarded("widths", lambda: run_widths_extra(flatA, flatB, K, bw, p64))
+    if "error" not in w:
+        summ["widths"] = {kind: {dt: [statistics.median(w[kind][dt]["roofline_pct"]), w[kind][dt]["min_pct"],
+                                      [i + 1 for i, p in enumerate(w[kind][dt]["roofline_pct"]) if p < 90.0]]
+                                 for dt in ("r64", "c64")} for kind in ("tsmttsm", "tsmm_beta0", "tsmm_beta1")}
+        summ["widths"]["what"] = "M=N=w, w=1..64: [median %, min %, widths below 90 %]"
+    sp = guarded("split", lambda: run_split_extra(flatA, flatB, K, bw))
+    if isinstance(sp, list):
+        summ["split"] = {"%s %dx%d %s" % (r["dtype"], r["M"], r["N"], r["dist"][:4]):
+                         [r["ms_split"], r["speedup"], float("%.2g" % r["oracle_entry_err_vs_norms"])]
+                         for r in sp}
+        summ["split"]["what"] = "[ms, speed-up over FP64, max sampled-entry error vs oracle / (|a_m||b_n|)]"
+    cb = guarded("cublas", lambda: run_cublas_extra(flatA, flatB, K, bw, p64))
+    if "value" in cb:
+        summ["cublas_tsmttsm_pct"] = round(cb["value"], 2)
+    gs = guarded("gs_step", lambda: run_gs_extra(flatA, flatB, K, bw, p64))
+    if "roofline_pct_all" in gs:
+        summ["gs_step_pct"] = round(gs["roofline_pct_all"], 2)
+    guarded("small_k_ramp", lambda: run_ramp_extra(flatA, flatB, bw, p64))
+    bt = guarded("batched", lambda: run_batched_extra(flatA, flatB))
+    if "separate_launches_ms" in bt:
+        summ["batched_ms"] = {k: round(bt[k], 1) for k in bt if k.endswith("_ms")}
+    return summ
 
 
 def main():
-    ap = argparse.ArgumentParser(description="TSMTTSM roofline sweep benchmark")
+    ap = argparse.ArgumentParser(description="TSMTTSM / TSMM roofline sweep benchmark")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--cpu-rows", type=int, default=1 << 17, help="rows of the CPU-oracle sample per config")
-    ap.add_argument("--ref-rows", type=int, default=1 << 14, help="rows per config per reference-arm step")
+    ap.add_argument("--cpu-rows", type=int, default=1 << 17, help="rows per call of the 1-thread CPU sample")
+    ap.add_argument("--cpu-rows-all", type=int, default=1 << 19, help="rows per call of the all-cores CPU sample")
+    ap.add_argument("--ref-rows", type=int, default=1 << 17, help="rows per call per reference-arm step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the split / TSMM / batched extras")
+    ap.add_argument("--no-extras", action="store_true", help="skip the per-width / split / batched extras")
+    ap.add_argument("--extras-out", default=None, help="also write every extra to this JSON file")
     ap.add_argument("--case", default=None, help="profile one config, e.g. c64:64x64")
     ap.add_argument("--k", type=int, default=1 << 20, help="rows for --case")
     ap.add_argument("--split", action="store_true", help="--case: use the split-precision path")
+    ap.add_argument("--tsmm", action="store_true", help="--case: TSMM instead of TSMTTSM")
+    ap.add_argument("--beta", type=float, default=0.0, help="--case --tsmm: beta")
     args = ap.parse_args()
     bw, bw_src = load_peaks()
     if args.case:

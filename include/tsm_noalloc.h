@@ -13,11 +13,16 @@
  * Scratch.  A file-scope device array of TSM_NOALLOC_SCRATCH_BYTES bytes
  * (16 MiB), present on every GPU that loads the library until the process
  * exits.  It holds the per-CTA partial sums of the deterministic reduction
- * and the reduction ticket.  The kernel runs one CTA per SM, so a call
- * needs  sm_count * M * N * (1 real | 2 complex) * 8  bytes of partials
- * (at most 152 * 64 * 64 * 2 * 8 = 9.5 MiB on a 152-SM GB300); a shape that
- * would need more than the array on a larger GPU returns
- * TSM_ERR_NOT_SUPPORTED and launches nothing.
+ * and the reduction ticket.  A call runs the kernel and grid that
+ * tsm_tsmttsm would run (tuning table, then heuristic) and, like it, a
+ * separate final reduction kernel when the partials are many.  When the
+ * partials of that grid,  grid * M * N * (1 real | 2 complex) * 8  bytes,
+ * do not fit the array, the grid is lowered to the largest multiple of the
+ * SM count that fits; results then differ from tsm_tsmttsm's in rounding
+ * only.  On a 152-SM GB300 every shape fits at one CTA per SM (at most
+ * 152 * 64 * 64 * 2 * 8 = 9.5 MiB); a shape that does not fit even at one
+ * CTA per SM (a larger GPU) returns TSM_ERR_NOT_SUPPORTED and launches
+ * nothing.
  *
  * Set-up.  The first call on each device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first

@@ -18,11 +18,15 @@ extern "C" {
 #endif
 
 /*
- * FP64 arithmetic peak in GFLOP/s (2 flops per FMA).  mode 0: scalar DFMA
- * chains (the FP64 pipe the plain products use); mode 1: FP64 tensor MMA
- * (mma.sync m8n8k4, 2*8*8*4 flops per warp instruction).  `iters` inner
- * iterations per thread (>= 1).  INVALID_VALUE on a bad mode, null output or
- * iters < 1.
+ * FP64 arithmetic peak in GFLOP/s (2 flops per FMA).  mode 0: DFMA on the
+ * FP64 pipe in the products' own form (a 4 x 4 register tile updated by
+ * register outer products, 16 independent chains per thread); mode 1: FP64
+ * tensor MMA (mma.sync m8n8k4, 2*8*8*4 flops per warp instruction); mode 2:
+ * DFMA chains x = x * m + a with compile-time constants m, a (an earlier
+ * form of the probe, kept for comparison).  608 CTAs of 256 threads on a
+ * 152-SM part; `iters` inner iterations per thread (>= 1); the best of
+ * three timed launches after one warm-up launch.  INVALID_VALUE on a bad
+ * mode, null output or iters < 1.
  */
 tsm_status tsm_probe_fp64(int mode, int64_t iters, double *gflops, tsm_stream_t stream);
 

@@ -68,16 +68,20 @@ extern "C" tsm_status tsm_tsmttsm_noalloc(tsm_op opA, tsm_dtype dtype, int M, in
                    ? TSM_OK
                    : TSM_ERR_LAUNCH;
 
-    // One CTA per SM; its partial sums must fit the array (the last 256
-    // bytes hold the ticket).
-    const int grid = di.sm_count;
-    const size_t need = (size_t)grid * M * N * (cplx ? 2 : 1) * sizeof(double);
-    if (need > (size_t)TSM_NOALLOC_SCRATCH_BYTES - 256) return TSM_ERR_NOT_SUPPORTED;
-
-    int variant = -1, unused_grid = 0;
-    if ((st = choose(TSM_KIND_TSMTTSM, dtype, M, N, K, &variant, &unused_grid)) != TSM_OK) return st;
+    int variant = -1, grid = 0;
+    if ((st = choose(TSM_KIND_TSMTTSM, dtype, M, N, K, &variant, &grid)) != TSM_OK) return st;
     const Variant* var = variant_at(TSM_KIND_TSMTTSM, variant);
     if (!var || !var->tsmttsm) return TSM_ERR_INTERNAL;
+
+    // The tuned grid, capped so that the CTA partial sums fit the array (its
+    // last 256 bytes hold the ticket); a capped grid stays a multiple of the
+    // SM count.  Only a shape whose partials do not fit even at one CTA per
+    // SM is refused.
+    const size_t per_cta = (size_t)M * N * (cplx ? 2 : 1) * sizeof(double);
+    const size_t max_ctas = ((size_t)TSM_NOALLOC_SCRATCH_BYTES - 256) / per_cta;
+    if (max_ctas < (size_t)di.sm_count) return TSM_ERR_NOT_SUPPORTED;
+    if (grid > 65535) grid = 65535;
+    if ((size_t)grid > max_ctas) grid = (int)(max_ctas / di.sm_count) * di.sm_count;
 
     void* scratch = nullptr;
     if ((st = scratch_address(&scratch)) != TSM_OK) return st;
@@ -103,6 +107,9 @@ extern "C" tsm_status tsm_tsmttsm_noalloc(tsm_op opA, tsm_dtype dtype, int M, in
     a.conj = (cplx && opA == TSM_OP_C) ? 1 : 0;
     a.ws = static_cast<double*>(scratch);
     a.ticket = ticket;
-    a.final_pass = 0;  // the last CTA sums the partials: no second launch
-    return var->tsmttsm(a, grid, s) == cudaSuccess ? TSM_OK : TSM_ERR_LAUNCH;
+    // many partials: a separate final kernel sums them (it allocates nothing)
+    a.final_pass = tsm_tsmttsm_kernels_per_call(dtype, M, N, grid) == 2 ? 1 : 0;
+    if (var->tsmttsm(a, grid, s) != cudaSuccess) return TSM_ERR_LAUNCH;
+    if (a.final_pass && launch_tsmttsm_final(a, grid, cplx, s) != cudaSuccess) return TSM_ERR_LAUNCH;
+    return TSM_OK;
 }

@@ -20,7 +20,8 @@ def _stream(stream):
 
 
 def fp64_peak(mode=0, iters=20000, stream=None):
-    """Measured FP64 GFLOP/s: mode 0 DFMA, mode 1 FP64 MMA."""
+    """Measured FP64 GFLOP/s: mode 0 DFMA register tile, mode 1 FP64 MMA,
+    mode 2 the constant-operand DFMA chain of the first probe."""
     out = ctypes.c_double()
     _lib.call("tsm_probe_fp64", mode, iters, ctypes.byref(out), _stream(stream))
     return out.value
