@@ -380,7 +380,7 @@ def measure_fp64_peak(local):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.2)
-    dfma = probe.fp64_peak(0, iters=40000)
+    dfma = probe.fp64_peak(0, iters=30000)
     dmma = probe.fp64_peak(1, iters=20000)
     chain = probe.fp64_peak(2, iters=40000)
     info = clocks.stop()

@@ -19,14 +19,17 @@ extern "C" {
 
 /*
  * FP64 arithmetic peak in GFLOP/s (2 flops per FMA).  mode 0: DFMA on the
- * FP64 pipe in the products' own form (a 4 x 4 register tile updated by
- * register outer products, 16 independent chains per thread); mode 1: FP64
- * tensor MMA (mma.sync m8n8k4, 2*8*8*4 flops per warp instruction); mode 2:
- * DFMA chains x = x * m + a with compile-time constants m, a (an earlier
- * form of the probe, kept for comparison).  608 CTAs of 256 threads on a
- * 152-SM part; `iters` inner iterations per thread (>= 1); the best of
- * three timed launches after one warm-up launch.  INVALID_VALUE on a bad
- * mode, null output or iters < 1.
+ * FP64 pipe in the products' own form (a 4 x 4 or 8 x 4 register tile
+ * updated by register outer products, 16 or 32 independent chains per
+ * thread), launched with 1, 2 and 4 CTAs of 256 threads per SM; the fastest
+ * of the six shapes is reported.  mode 1: FP64 tensor MMA (mma.sync
+ * m8n8k4, 2*8*8*4 flops per warp instruction); mode 2: DFMA chains
+ * x = x * m + a with compile-time constants m, a (an earlier form of the
+ * probe, kept for comparison); both with 4 CTAs of 256 threads per SM.
+ * `iters` sets the work (inner iterations per thread at 4 CTAs per SM and
+ * 16 chains; the other shapes do the same FMAs per SM).  Each shape: the
+ * best of two timed launches after one warm-up launch.  INVALID_VALUE on a
+ * bad mode, null output or iters < 1.
  */
 tsm_status tsm_probe_fp64(int mode, int64_t iters, double *gflops, tsm_stream_t stream);
 

@@ -78,6 +78,49 @@ def tile_for_width(w, cplx, cap=40, min_lanes=1):
     return None if best is None else (best[1], best[2])
 
 
+def tile_regs(tm, tn, cplx, rows=1):
+    """Rough register count of a TSMTTSM thread with a tm x tn tile: the
+    accumulators, the operands of `rows` rows in flight and about 24 for
+    addresses and the loop."""
+    c = 2 if cplx else 1
+    return 2 * c * (tm * tn + rows * (tm + tn)) + 24
+
+
+def warp_fill(w, tm, tn, block):
+    """Share of the FP64 issue slots a CTA of `block` threads spends on
+    useful FMAs for the square width w and tile tm x tn: its L = block // P
+    row lanes hold L * P active threads, every warp with at least one of
+    them issues all 32 lanes' FMAs (an idle lane of a partly filled warp
+    still takes its slot of this part's FP64 pipe), and the tile's padded
+    entries are wasted too."""
+    P = math.ceil(w / tm) * math.ceil(w / tn)
+    L = block // P
+    if L < 1:
+        return 0.0
+    return w * w * L / (math.ceil(L * P / 32) * 32 * tm * tn)
+
+
+def fullwarp_tile(w, cplx, cap=40):
+    """(T_M, T_N, block) for the square width w that maximises warp_fill
+    over tiles of at most `cap` accumulator doubles and CTAs of 128..1024
+    threads (multiples of 32) whose estimated registers fit one CTA per SM;
+    ties go to fewer registers, then to the block closest to 256."""
+    c = 2 if cplx else 1
+    best = None
+    for tm in range(1, w + 1):
+        for tn in range(1, w + 1):
+            if tm * tn * c > cap:
+                continue
+            r = tile_regs(tm, tn, cplx)
+            for block in range(128, 1025, 32):
+                if r * block > 65536 or r > 255:
+                    break
+                key = (-round(warp_fill(w, tm, tn, block), 3), r, abs(block - 256), tm)
+                if best is None or key < best[0]:
+                    best = (key, tm, tn, block)
+    return best[1], best[2], best[3]
+
+
 def tpr_options(N, cplx, k=2):
     """Up to k TSMM (threads per row t, results per thread npt) choices for
     N columns: the least padding npt t - N, then npt closest to 4 (the
@@ -129,8 +172,16 @@ def default_specs():
                 t2 = tile_for_width(w, cplx, min_lanes=2)
                 if t2 is not None and t2 != (tm, tn):
                     tiles.append((t2[0], t2[1], 4 if t2[0] * t2[1] <= 2 else (2 if t2[0] * t2[1] <= 8 else 1)))
-            for (a, b, u) in tiles:
-                tsmttsm.append(dict(cplx=cplx, M=w, N=w, TM=a, TN=b, U=u))
+            specs = [dict(cplx=cplx, M=w, N=w, TM=a, TN=b, U=u) for (a, b, u) in tiles]
+            # the tile and CTA size that keep every warp's lanes busy
+            # (warp_fill); added unless a 256-thread candidate already is it
+            fm, fn, fb = fullwarp_tile(w, cplx)
+            fu = 4 if fm * fn <= 2 else (2 if fm * fn <= 8 else 1)
+            while fu > 1 and tile_regs(fm, fn, cplx, fu) * fb > 65536:
+                fu //= 2
+            if not (fb == BLOCK and any((x["TM"], x["TN"]) == (fm, fn) for x in specs)):
+                specs.append(dict(cplx=cplx, M=w, N=w, TM=fm, TN=fn, U=fu, B=fb))
+            tsmttsm.extend(specs)
             for tpr, npt in tpr_options(w, cplx, 2):
                 tsmm.append(dict(cplx=cplx, M=w, N=w, TPR=tpr, U=2 if npt * c <= 8 else 1))
     tshapes = [(w, w) for w in SWEEP_SQUARE] + list(TSMM_OFFDIAG)
@@ -145,8 +196,9 @@ def default_specs():
 
 
 def _name_tsmttsm(s):
-    return "gen_tsmttsm_%s_m%dn%d_t%dx%d_u%d" % ("c64" if s["cplx"] else "r64", s["M"], s["N"],
+    name = "gen_tsmttsm_%s_m%dn%d_t%dx%d_u%d" % ("c64" if s["cplx"] else "r64", s["M"], s["N"],
                                                  s["TM"], s["TN"], s["U"])
+    return name + ("_b%d" % s["B"] if s.get("B", BLOCK) != BLOCK else "")
 
 
 def _name_tsmm(s):
@@ -157,10 +209,11 @@ def _name_tsmm(s):
 def emit_tsmttsm(s):
     """One TSMTTSM kernel for fixed M, N, tile and unroll."""
     M, N, TM, TN, U, cplx = s["M"], s["N"], s["TM"], s["TN"], s["U"], s["cplx"]
+    BLK = s.get("B", BLOCK)
     CC = 2 if cplx else 1
     PM, PN = math.ceil(M / TM), math.ceil(N / TN)
     P = PM * PN
-    L = BLOCK // P
+    L = BLK // P
     name = _name_tsmttsm(s)
     # entry i is always in range iff the largest pm (PM - 1) still fits
     gm = [(PM - 1) + i * PM >= M for i in range(TM)]
@@ -168,12 +221,12 @@ def emit_tsmttsm(s):
     o = []
     w = o.append
     w("template <bool CONJ>")
-    w("__global__ void __launch_bounds__(%d) %s(const TsmttsmArgs a) {" % (BLOCK, name))
+    w("__global__ void __launch_bounds__(%d) %s(const TsmttsmArgs a) {" % (BLK, name))
     w("    constexpr int PM = %d, PN = %d, P = %d, L = %d;" % (PM, PN, P, L))
     w("    const int t = threadIdx.x;")
     w("    const int lane = t / P, p = t - lane * P;")
     w("    const int pm = p % PM, pn = p / PM;")
-    w("    const bool active = %s;" % ("lane < L" if L * P < BLOCK else "true"))
+    w("    const bool active = %s;" % ("lane < L" if L * P < BLK else "true"))
     for i in range(TM):
         if gm[i]:
             w("    const bool gm%d = pm + %d < %d;" % (i, i * PM, M))
@@ -246,21 +299,21 @@ def emit_tsmttsm(s):
     w("    }")
     accs = ", ".join("c%d_%d_%d" % (i, j, c) for i in range(TM) for j in range(TN) for c in range(CC))
     w("    const double acc[%d] = {%s};" % (TM * TN * CC, accs))
-    w("    tsmttsm_finish<%d, %d, %d>(a, acc, PM, PN, L, lane, p, active);" % (TM, TN, CC))
+    w("    tsmttsm_finish<%d, %d, %d, %d>(a, acc, PM, PN, L, lane, p, active);" % (TM, TN, CC, BLK))
     w("}")
     w("")
     w("cudaError_t launch_%s(const TsmttsmArgs& a, int grid, cudaStream_t s) {" % name)
     if cplx:
-        w("    if (a.conj) %s<true><<<grid, %d, 0, s>>>(a);" % (name, BLOCK))
-        w("    else %s<false><<<grid, %d, 0, s>>>(a);" % (name, BLOCK))
+        w("    if (a.conj) %s<true><<<grid, %d, 0, s>>>(a);" % (name, BLK))
+        w("    else %s<false><<<grid, %d, 0, s>>>(a);" % (name, BLK))
     else:
-        w("    %s<false><<<grid, %d, 0, s>>>(a);" % (name, BLOCK))
+        w("    %s<false><<<grid, %d, 0, s>>>(a);" % (name, BLK))
     w("    return cudaGetLastError();")
     w("}")
     w("int occ_%s(int, int) {" % name)
     w("    int n = 0;")
     w("    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, %s<false>, %d, 0) != cudaSuccess) return 0;"
-      % (name, BLOCK))
+      % (name, BLK))
     w("    return n;")
     w("}")
     w("")
@@ -402,7 +455,8 @@ def _reg_tsmttsm(s):
             " v.info.kind = TSM_KIND_TSMTTSM; v.info.dtype = %d; v.info.fixed_m = %d; v.info.fixed_n = %d;"
             " v.info.tile_m = %d; v.info.tile_n = %d; v.info.unroll = %d; v.info.block = %d;"
             " v.info.generated = 1; v.tsmttsm = launch_%s; v.occupancy = occ_%s; t.push_back(v); }"
-            % (name, 1 if s["cplx"] else 0, s["M"], s["N"], s["TM"], s["TN"], s["U"], BLOCK, name, name))
+            % (name, 1 if s["cplx"] else 0, s["M"], s["N"], s["TM"], s["TN"], s["U"], s.get("B", BLOCK), name,
+               name))
 
 
 def _reg_tsmm(s):

@@ -164,11 +164,12 @@ __device__ __forceinline__ void tsmttsm_cross_cta(const TsmttsmArgs& a, double* 
 // Every order above depends only on (G, M, N, tile), so results repeat bit
 // for bit.
 // Kernels with a tile chosen at launch pass its size (tm <= TM, tn <= TN;
-// warp-uniform, so skipped entries cost nothing).
-template <int TM, int TN, int CC>
+// warp-uniform, so skipped entries cost nothing).  BLK is the kernel's CTA
+// size (L * P <= BLK).
+template <int TM, int TN, int CC, int BLK = kBlock>
 __device__ __forceinline__ void tsmttsm_finish(const TsmttsmArgs& a, const double* acc, int PM, int PN,
                                                int L, int lane, int p, bool active, int tm = TM, int tn = TN) {
-    __shared__ double red[kBlock * CC];
+    __shared__ double red[BLK * CC];
     __shared__ unsigned s_last;
     const int M = a.M, N = a.N;
     const int P = PM * PN;

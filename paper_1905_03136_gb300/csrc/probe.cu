@@ -8,30 +8,33 @@ namespace {
 
 constexpr int kChains = 16;  // independent FMA chains per thread
 
-// DFMA peak in the form the products run: a 4 x 4 register tile updated by
+// DFMA peak in the form the products run: a TM x 4 register tile updated by
 // the outer product of two register vectors (acc[m][n] += a[m] * b[n]), so
-// every operand is a register (no constant-bank operand) and 16 independent
-// accumulator chains per thread hide the pipe latency.  The operands come
-// from the kernel argument, so nothing can be folded at compile time.
+// every operand is a register (no constant-bank operand) and 4 TM
+// independent accumulator chains per thread hide the pipe latency.  The
+// operands come from the kernel argument, so nothing can be folded at
+// compile time.
+template <int TM>
 __global__ void k_dfma_tile(int64_t iters, double seed, double* out) {
-    double a[4], b[4], acc[4][4];
+    double a[TM], b[4], acc[TM][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        a[i] = seed + threadIdx.x * 1e-9 + i * 1e-3;
-        b[i] = seed - threadIdx.x * 1e-9 - i * 1e-3;
+    for (int i = 0; i < TM; ++i) a[i] = seed + threadIdx.x * 1e-9 + i * 1e-3;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[j] = seed - threadIdx.x * 1e-9 - j * 1e-3;
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-    }
-#pragma unroll 4
+#pragma unroll 2
     for (int64_t it = 0; it < iters; ++it) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     double s = 0.0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) s += acc[i][j];
     if (s == 12345.678) out[0] = s;  // keeps the chains alive
@@ -154,32 +157,48 @@ extern "C" tsm_status tsm_probe_fp64(int mode, int64_t iters, double* gflops, ts
     const int sm = device_info().sm_count;
     double* dummy = nullptr;
     if (cudaMalloc(&dummy, 64) != cudaSuccess) return TSM_ERR_ALLOC;
-    const int blocks = sm * 4, threads = 256;
     Timer t(s);
     if (!t.ok) {
         cudaFree(dummy);
         return TSM_ERR_LAUNCH;
     }
-    float best = 1e30f;
-    for (int rep = 0; rep < 4; ++rep) {  // the first pass warms up the clocks
-        t.start();
-        if (mode == 0)
-            k_dfma_tile<<<blocks, threads, 0, s>>>(iters, 1.0, dummy);
-        else if (mode == 1)
-            k_dmma_peak<<<blocks, threads, 0, s>>>(iters, 1.0, dummy);
+    // mode 0 tries 1, 2 and 4 CTAs of 256 threads per SM with 16 and 32
+    // chains per thread (the products run 1-2 CTAs of 256 threads per SM)
+    // and keeps the fastest; modes 1 and 2 run 4 CTAs per SM
+    double best_gflops = 0.0;
+    const int nshape = mode == 0 ? 6 : 1;
+    for (int shape = 0; shape < nshape; ++shape) {
+        const int cps = mode == 0 ? (1 << (shape % 3)) : 4;
+        const int tm = mode == 0 && shape >= 3 ? 8 : 4;
+        const int blocks = sm * cps, threads = 256;
+        // the same number of FMAs per SM for every shape
+        const int64_t it = mode == 0 ? iters * 4 / cps * 4 / tm : iters;
+        float best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {  // the first pass warms up the clocks
+            t.start();
+            if (mode == 0 && tm == 4)
+                k_dfma_tile<4><<<blocks, threads, 0, s>>>(it, 1.0, dummy);
+            else if (mode == 0)
+                k_dfma_tile<8><<<blocks, threads, 0, s>>>(it, 1.0, dummy);
+            else if (mode == 1)
+                k_dmma_peak<<<blocks, threads, 0, s>>>(it, 1.0, dummy);
+            else
+                k_dfma_chain<<<blocks, threads, 0, s>>>(it, 1.0, dummy);
+            const float ms = t.stop();
+            if (rep > 0 && ms > 0.f && ms < best) best = ms;
+        }
+        if (best >= 1e29f) break;
+        double flops;
+        if (mode == 1)
+            flops = 2.0 * 8 * 8 * 4 * 4 * (double)it * blocks * (threads / 32);
         else
-            k_dfma_chain<<<blocks, threads, 0, s>>>(iters, 1.0, dummy);
-        const float ms = t.stop();
-        if (rep > 0 && ms > 0.f && ms < best) best = ms;
+            flops = 2.0 * (mode == 0 ? 4 * tm : kChains) * (double)it * blocks * threads;  // 2 flops per FMA
+        const double g = flops / (best * 1e-3) / 1e9;
+        if (g > best_gflops) best_gflops = g;
     }
-    double flops;
-    if (mode == 1)
-        flops = 2.0 * 8 * 8 * 4 * 4 * (double)iters * blocks * (threads / 32);
-    else
-        flops = 2.0 * kChains * (double)iters * blocks * threads;  // 2 flops per FMA
     cudaFree(dummy);
-    if (best >= 1e29f || cudaGetLastError() != cudaSuccess) return TSM_ERR_LAUNCH;
-    *gflops = flops / (best * 1e-3) / 1e9;
+    if (best_gflops <= 0.0 || cudaGetLastError() != cudaSuccess) return TSM_ERR_LAUNCH;
+    *gflops = best_gflops;
     return TSM_OK;
 }
 

@@ -140,20 +140,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 // Bounded wait: false if the phase did not complete within `timeout` SM
 // cycles (the error word is then set to `code`), or if another warp raised
 // the CTA's abort flag meanwhile (`abort_flag` may be null: wait regardless).
+// mbarrier.try_wait itself suspends the warp until the phase completes or a
+// hardware time limit passes, so the loop wakes as soon as the barrier
+// flips; only waits longer than 2^16 cycles (never in steady state) add a
+// sleep to leave issue slots to the working warps.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long timeout, int* err,
                                           int code, const volatile int* abort_flag) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
-    unsigned ns = 16;  // back off so waiting warps leave issue slots to working ones
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
         if (abort_flag && *abort_flag) return false;
-        if (clock64() - t0 > timeout) {
+        const long long dt = clock64() - t0;
+        if (dt > timeout) {
             atomicCAS(err, 0, code);
             return false;
         }
-        __nanosleep(ns);
-        if (ns < 256) ns <<= 1;
+        if (dt > 65536) __nanosleep(256);
     }
 }
 __device__ __forceinline__ void fence_proxy_async() {

@@ -68,3 +68,45 @@ def test_emitted_kernels_guard_only_border_entries():
     src = codegen.emit_tsmttsm(dict(cplx=False, M=7, N=7, TM=4, TN=4, U=1))
     guards = sorted(l.strip() for l in src.splitlines() if "const bool g" in l)
     assert guards == ["const bool gm3 = pm + 6 < 7;", "const bool gn3 = pn + 6 < 7;"]
+
+
+def test_warp_fill_counts_partly_filled_warps():
+    # width 26, tile 13 x 2: P = 26 threads per row lane; 256 threads hold 9
+    # lanes (234 active), the eighth warp has 10 active lanes but issues all
+    # 32, so 234 of 256 FMA slots are useful
+    assert abs(codegen.warp_fill(26, 13, 2, 256) - 234 / 256) < 1e-12
+    # 416 threads hold 16 lanes: 13 full warps
+    assert codegen.warp_fill(26, 13, 2, 416) == 1.0
+    # padding counts too: width 7 with 4 x 4 tiles (P = 4, 64 lanes)
+    assert abs(codegen.warp_fill(7, 4, 4, 256) - 49 / 64) < 1e-12
+    assert codegen.warp_fill(64, 1, 1, 256) == 0.0  # 4096 threads per lane do not fit
+
+
+def test_fullwarp_tile_for_every_width():
+    """Every square width gets a tile and CTA size that keeps at least 93 %
+    of the FP64 issue slots useful (most widths 96-100 %), within 1024
+    threads, a multiple of 32, and one CTA per SM by the register estimate;
+    the generated set holds that kernel for every non-sweep width."""
+    tsmttsm, _ = codegen.default_specs()
+    names = {codegen._name_tsmttsm(s) for s in tsmttsm}
+    fills = []
+    for cplx in (False, True):
+        c = 2 if cplx else 1
+        for w in range(1, 65):
+            tm, tn, blk = codegen.fullwarp_tile(w, cplx)
+            assert tm * tn * c <= 40 and blk % 32 == 0 and 128 <= blk <= 1024
+            assert codegen.tile_regs(tm, tn, cplx) * blk <= 65536
+            f = codegen.warp_fill(w, tm, tn, blk)
+            fills.append(f)
+            assert f >= 0.93, (w, cplx, tm, tn, blk, f)
+            # never worse than the 256-thread least-padded tile
+            a, b = codegen.tile_for_width(w, cplx)
+            assert f >= codegen.warp_fill(w, a, b, codegen.BLOCK) - 1e-9
+            if w not in codegen.SWEEP_SQUARE:
+                u = 4 if tm * tn <= 2 else (2 if tm * tn <= 8 else 1)
+                while u > 1 and codegen.tile_regs(tm, tn, cplx, u) * blk > 65536:
+                    u //= 2
+                spec = dict(cplx=cplx, M=w, N=w, TM=tm, TN=tn, U=u, B=blk)
+                assert codegen._name_tsmttsm(spec if blk != codegen.BLOCK else
+                                             dict(spec, B=codegen.BLOCK)) in names, (w, cplx)
+    assert sorted(fills)[len(fills) // 2] >= 0.99
