@@ -135,6 +135,27 @@ def tpr_options(N, cplx, k=2):
     return [(t, npt) for _, t, npt in opts[:k]]
 
 
+def tsmm_fill(N, tpr, npt, block):
+    """Share of the FP64 issue slots a TSMM CTA of `block` threads spends on
+    useful FMAs: block // tpr rows per step, every warp with an active
+    thread issues all 32 lanes, and npt * tpr - N padded result slots are
+    wasted."""
+    rpc = block // tpr
+    return N * rpc / (math.ceil(rpc * tpr / 32) * 32 * npt)
+
+
+def tsmm_block(N, tpr, npt):
+    """CTA size for a TSMM kernel with `tpr` threads per row: a multiple of
+    lcm(tpr, 32) (every warp full) in 128..1024 closest to 256 when that
+    fills the warps better than 256 threads, else 256."""
+    lcm = tpr * 32 // math.gcd(tpr, 32)
+    sizes = [lcm * j for j in range(1, 1024 // lcm + 1) if lcm * j >= 128]
+    if not sizes:
+        return BLOCK
+    b = min(sizes, key=lambda x: (abs(x - BLOCK), x))
+    return b if tsmm_fill(N, tpr, npt, b) > tsmm_fill(N, tpr, npt, BLOCK) + 1e-9 else BLOCK
+
+
 def tpr_for_width(N, cplx):
     """The first of tpr_options: (threads per row, results per thread)."""
     return tpr_options(N, cplx, 1)[0]
@@ -183,7 +204,11 @@ def default_specs():
                 specs.append(dict(cplx=cplx, M=w, N=w, TM=fm, TN=fn, U=fu, B=fb))
             tsmttsm.extend(specs)
             for tpr, npt in tpr_options(w, cplx, 2):
-                tsmm.append(dict(cplx=cplx, M=w, N=w, TPR=tpr, U=2 if npt * c <= 8 else 1))
+                spec = dict(cplx=cplx, M=w, N=w, TPR=tpr, U=2 if npt * c <= 8 else 1)
+                blk = tsmm_block(w, tpr, npt)
+                if blk != BLOCK:
+                    spec["B"] = blk
+                tsmm.append(spec)
     tshapes = [(w, w) for w in SWEEP_SQUARE] + list(TSMM_OFFDIAG)
     for cplx in (False, True):
         for (M, N) in tshapes:
@@ -202,8 +227,9 @@ def _name_tsmttsm(s):
 
 
 def _name_tsmm(s):
-    return "gen_tsmm_%s_m%dn%d_tpr%d_u%d" % ("c64" if s["cplx"] else "r64", s["M"], s["N"],
+    name = "gen_tsmm_%s_m%dn%d_tpr%d_u%d" % ("c64" if s["cplx"] else "r64", s["M"], s["N"],
                                              s["TPR"], s["U"])
+    return name + ("_b%d" % s["B"] if s.get("B", BLOCK) != BLOCK else "")
 
 
 def emit_tsmttsm(s):
@@ -324,9 +350,10 @@ def emit_tsmm(s):
     """One TSMM kernel for fixed M, N, threads per row and unroll; C comes
     from shared memory (Sec. 4.2), the m loop is fully unrolled."""
     M, N, TPR, U, cplx = s["M"], s["N"], s["TPR"], s["U"], s["cplx"]
+    BLK = s.get("B", BLOCK)
     CC = 2 if cplx else 1
     NPT = math.ceil(N / TPR)
-    RPC = BLOCK // TPR
+    RPC = BLK // TPR
     name = _name_tsmm(s)
     gn = [(TPR - 1) + j * TPR >= N for j in range(NPT)]
     o = []
@@ -338,13 +365,13 @@ def emit_tsmm(s):
     split = TPR <= 8
     if split:
         w("template <bool GEN>")
-    w("__global__ void __launch_bounds__(%d) %s(const TsmmArgs a) {" % (BLOCK, name))
+    w("__global__ void __launch_bounds__(%d) %s(const TsmmArgs a) {" % (BLK, name))
     w("    extern __shared__ double cs[];")
     w("    tsmm_stage_c<%d>(a, cs);" % CC)
     w("    constexpr int TPR = %d, RPC = %d;" % (TPR, RPC))
     w("    const int r = threadIdx.x / TPR, q = threadIdx.x - r * TPR;")
     # threads past RPC * TPR (TPR not dividing the block) hold no row
-    live = "" if BLOCK % TPR == 0 else "r < RPC && "
+    live = "" if BLK % TPR == 0 else "r < RPC && "
     for j in range(NPT):
         if gn[j]:
             w("    const bool gn%d = q + %d < %d;" % (j, j * TPR, N))
@@ -416,15 +443,15 @@ def emit_tsmm(s):
               "cudaFuncAttributeMaxDynamicSharedMemorySize, %d);" % (name, name, smem))
             w("    if (e != cudaSuccess) return e;")
         w("    if (gen)")
-        w("        %s<true><<<grid, %d, %d, s>>>(a);" % (name, BLOCK, smem))
+        w("        %s<true><<<grid, %d, %d, s>>>(a);" % (name, BLK, smem))
         w("    else")
-        w("        %s<false><<<grid, %d, %d, s>>>(a);" % (name, BLOCK, smem))
+        w("        %s<false><<<grid, %d, %d, s>>>(a);" % (name, BLK, smem))
     else:
         if smem > 48 * 1024:
             w("    cudaError_t e = cudaFuncSetAttribute(%s, cudaFuncAttributeMaxDynamicSharedMemorySize, %d);"
               % (name, smem))
             w("    if (e != cudaSuccess) return e;")
-        w("    %s<<<grid, %d, %d, s>>>(a);" % (name, BLOCK, smem))
+        w("    %s<<<grid, %d, %d, s>>>(a);" % (name, BLK, smem))
     w("    return cudaGetLastError();")
     w("}")
     w("int occ_%s(int, int) {" % name)
@@ -433,7 +460,7 @@ def emit_tsmm(s):
           " return 0;" % (base, smem))
     w("    int n = 0;")
     w("    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, %s, %d, %d) != cudaSuccess) return 0;"
-      % (base, BLOCK, smem))
+      % (base, BLK, smem))
     w("    return n;")
     w("}")
     w("")
@@ -466,7 +493,8 @@ def _reg_tsmm(s):
             " v.info.kind = TSM_KIND_TSMM; v.info.dtype = %d; v.info.fixed_m = %d; v.info.fixed_n = %d;"
             " v.info.tile_n = %d; v.info.threads_per_row = %d; v.info.unroll = %d; v.info.block = %d;"
             " v.info.generated = 1; v.tsmm = launch_%s; v.occupancy = occ_%s; m.push_back(v); }"
-            % (name, 1 if s["cplx"] else 0, s["M"], s["N"], npt, s["TPR"], s["U"], BLOCK, name, name))
+            % (name, 1 if s["cplx"] else 0, s["M"], s["N"], npt, s["TPR"], s["U"], s.get("B", BLOCK), name,
+               name))
 
 
 def generate(out_dir, shards=16, specs=None):
