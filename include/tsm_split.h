@@ -15,13 +15,18 @@
  * are recombined and reduced over K in binary64.  Complex data is handled
  * as the real product of the interleaved (re, im) columns.
  *
- * Accuracy: each input keeps 47 bits below its column's running maximum and
- * slice products with combined weight below 2^-54 are dropped, so
- * |C_split - C_exact| is a few units of 2^-47 relative to sum |a||b| per
- * entry; the normwise relative error against the FP64 oracle is about
- * 1e-13 on uniform and log-uniform inputs.  Inputs must be finite (NaN/Inf
- * are not propagated; use tsm_tsmttsm for them).  Results are
- * deterministic for a fixed problem and device.
+ * Accuracy: with S slices each input keeps 8S - 1 bits below its column's
+ * running maximum and slice products of combined weight below 2^-(8S+6)
+ * are dropped, so |C_split - C_exact| is a few units of 2^-(8S-1) relative
+ * to sum |a||b| per entry.  S = 6 (tsm_tsmttsm_split): normwise relative
+ * error against the FP64 oracle about 1e-14 on uniform and log-uniform
+ * inputs, within the 1e-12 bar of the FP64 path; S = 5: about 4e-12;
+ * S = 4: about 1e-9 (fewer tensor-core products, fewer accumulator
+ * columns, faster).  Inputs that are small integers (or any values with at
+ * most 8S - 1 significant bits below the column maximum) give the exact
+ * result.  Inputs must be finite (NaN/Inf are not propagated; use
+ * tsm_tsmttsm for them).  Results are deterministic for a fixed problem,
+ * slice count and device.
  *
  * Arguments, layout, ownership and argument errors as tsm_tsmttsm (tsm.h);
  * any alignment and leading dimension is accepted.  Work is asynchronous on
@@ -43,6 +48,29 @@ tsm_status tsm_tsmttsm_split(tsm_op opA, tsm_dtype dtype, int M, int N,
                              int64_t lda, const void *B, int64_t ldb,
                              const double *beta, void *C, int64_t ldc,
                              tsm_stream_t stream);
+
+/*
+ * How inputs are split for the tensor cores.  TSM_SPLIT_DIGITS_F16: signed
+ * 8-bit digits held exactly in fp16, products on tcgen05 kind::f16 with
+ * FP32 accumulation (the only kind on sm_103a: the toolchain rejects
+ * kind::i8 there, and bf16 or fp8 digits would hold fewer bits per slice
+ * for the same product rate).
+ */
+typedef enum { TSM_SPLIT_DIGITS_F16 = 0 } tsm_split_kind;
+
+/*
+ * tsm_tsmttsm_split with the precision knobs: `kind` (TSM_SPLIT_DIGITS_F16)
+ * and `slices` S in [4, 6] per input (tsm_tsmttsm_split is S = 6).  Fewer
+ * slices trade accuracy (see above) for fewer tensor-core products per row
+ * (S (S + 1) / 2 digit pairs).  Errors: as tsm_tsmttsm_split; an unknown
+ * kind -> INVALID_VALUE; slices outside [4, 6] -> NOT_SUPPORTED.
+ */
+tsm_status tsm_tsmttsm_split_ex(tsm_op opA, tsm_dtype dtype, int M, int N,
+                                int64_t K, const double *alpha, const void *A,
+                                int64_t lda, const void *B, int64_t ldb,
+                                const double *beta, void *C, int64_t ldc,
+                                tsm_split_kind kind, int slices,
+                                tsm_stream_t stream);
 
 /*
  * Launch plan of tsm_tsmttsm_split for a shape (no work is done).  Narrow
@@ -67,6 +95,11 @@ typedef struct {
 
 tsm_status tsm_split_plan(tsm_dtype dtype, int M, int N, int64_t K,
                           tsm_split_plan_info *info);
+
+/* The plan of tsm_tsmttsm_split_ex with `slices` S (tsm_split_plan is
+ * S = 6).  slices outside [4, 6] -> NOT_SUPPORTED, else as tsm_split_plan. */
+tsm_status tsm_split_plan_ex(tsm_dtype dtype, int M, int N, int64_t K, int slices,
+                             tsm_split_plan_info *info);
 
 /*
  * Synchronizes `stream` and reports whether the most recent

@@ -68,7 +68,7 @@ namespace split {
 
 constexpr int KSTEP = 16;           // rows per MMA (16-bit inputs: K = 16)
 constexpr int TILE_STEPS = 16;      // steps per exact accumulation tile (256 rows)
-constexpr int NSLICE = 6;           // 8-bit slices per input
+constexpr int NSLICE_MAX = 6;       // 8-bit slices per input: S in [4, 6], a template parameter
 constexpr int NDIG_MAX = 6;         // digit stages (converters -> MMA): as many as fit, up to this
 constexpr int NEXP = 4;             // exponent snapshot ring (MMA warp -> epilogue)
 constexpr int MAX_MMAS = 9;         // MMAs per step (six slices of X against the Y slices, N <= 256 each)
@@ -233,13 +233,13 @@ constexpr uint32_t kSmemPerSM = 228u * 1024u;   // shared by the CTAs of an SM, 
 constexpr uint32_t kMiscBytes = 256u;
 
 __host__ __device__ inline Layout make_layout(int P, int Qp, int Qw, int stacked, uint32_t budget,
-                                              uint32_t floor_bytes) {
+                                              uint32_t floor_bytes, int S) {
     Layout L;
-    L.nrb = stacked ? 3 : 6;
+    L.nrb = stacked ? (S + 1) / 2 : S;
     L.units = 32 * ((((P + 7) & ~7) + Qw + 7) / 8);  // 4 units per column slot, 8 slots per group of 32
     L.ne = P + Qp;
     L.a_bytes = (uint32_t)L.nrb * 4096u;
-    L.b_bytes = (uint32_t)NSLICE * Qp * 32u;
+    L.b_bytes = (uint32_t)S * Qp * 32u;
     L.stage = ((L.a_bytes + L.b_bytes) + 1023u) & ~1023u;
     const uint32_t acc = (uint32_t)Qp * 128u * 8u;
     const uint32_t exps = (uint32_t)L.ne * 4u;
@@ -274,35 +274,39 @@ static_assert(M_TILE_INFO + 4 <= (int)kMiscBytes, "misc area");
 
 // ------------------------------------------------------------ digit maths
 
-// |x| as a fixed-point integer with 47 bits below 2^e (truncated), plus the
-// five low bytes biased by 0x80 so that they read back as balanced digits:
-// returns Y = X + 0x8080808080 where X = floor(|x| 2^(47-e)) < 2^47.  The
-// six base-256 digits of X = sum_s d_s 2^(40-8s) are d_0 = byte 5 of Y in
-// [0, 128] and d_s = byte (5-s) of Y - 128 in [-128, 127] for s >= 1.
-// Requires |x| < 2^e; subnormals are exact (no implicit bit); values below
-// the column's range give 0 (the shift is clamped to 63).
-__device__ __forceinline__ unsigned long long fixed47(double x, int e, uint32_t* sign) {
+// |x| as a fixed-point integer with 8S - 1 bits below 2^e (truncated), plus
+// the S - 1 low bytes biased by 0x80 so that they read back as balanced
+// digits: returns Y = X + 0x80...80 where X = floor(|x| 2^(8S-1-e)) <
+// 2^(8S-1).  The S base-256 digits of X = sum_s d_s 2^(8(S-1-s)) are
+// d_0 = byte S-1 of Y in [0, 128] and d_s = byte (S-1-s) of Y - 128 in
+// [-128, 127] for s >= 1.  Requires |x| < 2^e; subnormals are exact (no
+// implicit bit); values below the column's range give 0 (the shift is
+// clamped to 63).
+template <int S>
+__device__ __forceinline__ unsigned long long fixed_digits(double x, int e, uint32_t* sign) {
+    constexpr unsigned long long kBias = ((1ull << (8 * (S - 1))) - 1) / 255 * 0x80;  // 0x80 in S-1 bytes
     const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
     const uint32_t hi = (uint32_t)(bits >> 32);
     *sign = hi & 0x80000000u;
     const int ef = (int)((hi >> 20) & 0x7FFu);
     const uint32_t mhi = (hi & 0xFFFFFu) | (ef ? 0x100000u : 0u);
     const unsigned long long mant = ((unsigned long long)mhi << 32) | (uint32_t)bits;
-    const int sh = min(e + 1028 - max(ef, 1), 63);
-    return (mant >> sh) + 0x8080808080ull;
+    const int sh = min(e + 1076 - 8 * S - max(ef, 1), 63);
+    return (mant >> sh) + kBias;
 }
 
-// The six fp16 slices of two values a (row r) and b (row r + 1) of one
+// The S fp16 slices of two values a (row r) and b (row r + 1) of one
 // column, packed per slice as (a, b) in one 32-bit word, sign applied.  A
 // digit byte placed under the fp16 exponent of 1024 (0x64XX) is 1024 + byte
 // exactly.  Byte permutes gather the digit bytes of both values two slices at
 // a time and place them under 0x64; one packed fused multiply-add then forms
 // sign * (1024 + byte) - sign * bias, bias = 1024 for the top digit and 1152
 // (1024 + 128) for the balanced low digits: exact, since every result is a
-// small integer.
+// small integer.  Slice s is byte S - 1 - s of Y.
+template <int S>
 __device__ __forceinline__ void split_pair(double xa, double xb, int e, uint32_t* w) {
     uint32_t sa, sb;
-    const unsigned long long ya = fixed47(xa, e, &sa), yb = fixed47(xb, e, &sb);
+    const unsigned long long ya = fixed_digits<S>(xa, e, &sa), yb = fixed_digits<S>(xb, e, &sb);
     const uint32_t alo = (uint32_t)ya, ahi = (uint32_t)(ya >> 32);
     const uint32_t blo = (uint32_t)yb, bhi = (uint32_t)(yb >> 32);
     const uint32_t sg = (sa >> 16) | sb;       // sign of a in bit 15, of b in bit 31
@@ -320,30 +324,35 @@ __device__ __forceinline__ void split_pair(double xa, double xb, int e, uint32_t
                             *reinterpret_cast<const __half2*>(&add));
         return *reinterpret_cast<uint32_t*>(&h);
     };
-    w[0] = fin(m45, 0x4342, c_top);  // byte 5
-    w[1] = fin(m45, 0x4140, c_low);  // byte 4
-    w[2] = fin(m23, 0x4342, c_low);  // byte 3
-    w[3] = fin(m23, 0x4140, c_low);  // byte 2
-    w[4] = fin(m01, 0x4342, c_low);  // byte 1
-    w[5] = fin(m01, 0x4140, c_low);  // byte 0
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl) {
+        const int y = S - 1 - sl;  // byte of Y
+        const uint32_t pair = y >= 4 ? m45 : (y >= 2 ? m23 : m01);
+        w[sl] = fin(pair, (y & 1) ? 0x4342u : 0x4140u, sl == 0 ? c_top : c_low);
+    }
 }
 
-// W = sum_d P_d 2^(8(5-d)) for accumulator entry qq of the six blocks v[j]
-// (tensor-memory words, FP32 integers): block j holds weight d = j + H (rows of
-// the second stacked slice: H = 1; their d = 6 block is dropped).  Split as
-// 2^32 (P_0 2^8 + P_1) + P_2 2^24 + P_3 2^16 + P_4 2^8 + P_5: |P_0| <= 2^22
-// and |P_1| <= 2^23 keep the first part in 31 bits, the rest are exact 64-bit
-// multiply-adds.
-template <int H>
-__device__ __forceinline__ long long combine_w(const uint32_t (&v)[NSLICE][8], int qq) {
-    int pd[NSLICE];
+// W = sum_d P_d 2^(8(S-1-d)) for accumulator entry qq of the S blocks v[j]
+// (tensor-memory words, FP32 integers): block j holds weight d = j + H (rows
+// of the second stacked slice: H = 1; their d = S block is dropped).  The
+// terms shifted by 32 or more bits (P_0 2^8 + P_1 for S = 6, P_0 for S = 5)
+// are summed in 32 bits (|P_0| <= 2^22, |P_1| <= 2^23), the rest are exact
+// 64-bit multiply-adds.
+template <int H, int S>
+__device__ __forceinline__ long long combine_w(const uint32_t (&v)[S][8], int qq) {
+    int pd[S];
 #pragma unroll
-    for (int d = 0; d < NSLICE; ++d) pd[d] = d >= H ? __float2int_rn(__uint_as_float(v[d - H][qq])) : 0;
-    long long lo = (long long)pd[5];
-    lo += (long long)pd[4] * 256;
-    lo += (long long)pd[3] * 65536;
-    lo += (long long)pd[2] * 16777216;
-    const int hi = pd[0] * 256 + pd[1];
+    for (int d = 0; d < S; ++d) pd[d] = d >= H ? __float2int_rn(__uint_as_float(v[d - H][qq])) : 0;
+    long long lo = 0;
+    int hi = 0;
+#pragma unroll
+    for (int d = 0; d < S; ++d) {
+        const int sh = 8 * (S - 1 - d);
+        if (sh >= 32)
+            hi += pd[d] * (1 << (sh - 32));
+        else
+            lo += (long long)pd[d] * (1ll << sh);
+    }
     return (long long)((unsigned long long)lo + ((unsigned long long)(unsigned int)hi << 32));
 }
 
@@ -362,7 +371,7 @@ __device__ __forceinline__ uint32_t kmajor_off(int r, int g) {
 
 // ------------------------------------------------------------ the kernel
 
-template <int PER>
+template <int PER, int S>
 __global__ void __launch_bounds__(block_threads<PER>(), 1) k_split(const Params prm) {
     constexpr int DEPTH = Conv<PER>::DEPTH;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -375,7 +384,7 @@ __global__ void __launch_bounds__(block_threads<PER>(), 1) k_split(const Params 
     const int Qp = prm.Qp;
     const int64_t Ktot = prm.K;
     const int stacked = prm.stacked;
-    const Layout L = make_layout(P, Qp, Qw, stacked, (uint32_t)prm.smem_budget, (uint32_t)prm.smem_floor);
+    const Layout L = make_layout(P, Qp, Qw, stacked, (uint32_t)prm.smem_budget, (uint32_t)prm.smem_floor, S);
     const int NE = L.ne, ndig = L.ndig;
     unsigned char* dig = smem + L.dig_off;
     long long* iacc = reinterpret_cast<long long*>(smem + L.acc_off);
@@ -523,16 +532,16 @@ __global__ void __launch_bounds__(block_threads<PER>(), 1) k_split(const Params 
             for (int i = 0; i < PER; ++i) {
                 if (!valid[i]) continue;
                 if (owner[i]) ex[col[i]] = e[i];
-                uint32_t w[NSLICE][2];
+                uint32_t w[S][2];
 #pragma unroll
                 for (int r = 0; r < 4; r += 2) {
-                    uint32_t wp[NSLICE];
-                    split_pair(v[i][r], v[i][r + 1], e[i], wp);
+                    uint32_t wp[S];
+                    split_pair<S>(v[i][r], v[i][r + 1], e[i], wp);
 #pragma unroll
-                    for (int sl = 0; sl < NSLICE; ++sl) w[sl][r >> 1] = wp[sl];
+                    for (int sl = 0; sl < S; ++sl) w[sl][r >> 1] = wp[sl];
                 }
 #pragma unroll
-                for (int sl = 0; sl < NSLICE; ++sl)
+                for (int sl = 0; sl < S; ++sl)
                     *reinterpret_cast<uint2*>(stage + off0[i] + sl * dsl[i]) = make_uint2(w[sl][0], w[sl][1]);
             }
             fence_proxy_async();
@@ -583,7 +592,7 @@ __global__ void __launch_bounds__(block_threads<PER>(), 1) k_split(const Params 
 #pragma unroll
             for (int j = 0; j < MAX_MMAS; ++j) {
                 const int s_a = stacked ? 2 * rb : rb;  // first slice index of this row block
-                const int nt = NSLICE - s_a;            // slices t with s_a + t <= 5
+                const int nt = S - s_a;                 // slices t with s_a + t <= S - 1
                 const bool live = rb < L.nrb;
                 const int cnt = min(maxs, nt - t0);
                 adesc[j] = smem_desc(dig_a + (uint32_t)rb * 4096u, 128, 256);
@@ -709,7 +718,7 @@ __global__ void __launch_bounds__(block_threads<PER>(), 1) k_split(const Params 
                 const long long a = iacc[q * 128 + row];
                 if (a == 0) continue;
                 iacc[q * 128 + row] = 0;
-                flush[q * 128 + row] += scaled(a, epf + exs[P + q] - 54);
+                flush[q * 128 + row] += scaled(a, epf + exs[P + q] - (8 * S + 6));
             }
         };
         int prev_slot = -1;
@@ -733,22 +742,22 @@ __global__ void __launch_bounds__(block_threads<PER>(), 1) k_split(const Params 
             auto drain = [&](auto half_tag) {
                 constexpr int H = decltype(half_tag)::value;
                 for (int qb = qlo; qb < qhi; qb += 8) {
-                    uint32_t v[NSLICE][8];
+                    uint32_t v[S][8];
 #pragma unroll
-                    for (int j = 0; j < NSLICE; ++j)
+                    for (int j = 0; j < S; ++j)
                         tmem_ld8(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(j * Qp + qb), v[j]);
                     tmem_wait_ld();
 #pragma unroll
                     for (int qq = 0; qq < 8; ++qq) {
                         const int q = qb + qq;
                         if (!prow || q >= Qw) continue;
-                        const long long W = combine_w<H>(v, qq);
+                        const long long W = combine_w<H, S>(v, qq);
                         if (W == 0) continue;
                         long long* ap = &iacc[q * 128 + row];
                         const long long a = *ap;
                         long long sum = (long long)((unsigned long long)a + (unsigned long long)W);
                         if (((a ^ sum) & (W ^ sum)) < 0) {  // would overflow: move a to binary64
-                            flush[q * 128 + row] += scaled(a, ep + ex[P + q] - 54);
+                            flush[q * 128 + row] += scaled(a, ep + ex[P + q] - (8 * S + 6));
                             sum = W;
                         }
                         *ap = sum;
@@ -831,11 +840,11 @@ __global__ void k_split_combine(const double* ws, int n_kr, int P, int Q, int M,
 long long g_timeout = kDefaultTimeout;
 
 // MMAs per step for a chunk width Qp: the kernel builds at most MAX_MMAS.
-int count_mmas(int stacked, int Qp) {
+int count_mmas(int stacked, int Qp, int S) {
     const int maxs = 256 / Qp;
     int n = 0;
-    for (int rb = 0; rb < (stacked ? 3 : 6); ++rb) {
-        const int nt = NSLICE - (stacked ? 2 * rb : rb);
+    for (int rb = 0; rb < (stacked ? (S + 1) / 2 : S); ++rb) {
+        const int nt = S - (stacked ? 2 * rb : rb);
         n += (nt + maxs - 1) / maxs;
     }
     return n;
@@ -856,13 +865,23 @@ namespace split {
 struct Plan {
     Params prm;     // shape fields filled; pointers, workspace and timeout are the caller's
     Layout L;
+    int S = 6;      // slices per input
     int per = 1;    // converter units per thread
     int cps = 0;    // CTAs per SM
     int threads = 0;
     const void* fn = nullptr;
 };
 
-tsm_status make_plan(int cplx, int M, int N, int64_t K, Plan* pl) {
+// The kernel instantiation for (units per thread, slices).
+const void* kernel_for(int per, int S) {
+    if (per == 1) return S == 4 ? (const void*)k_split<1, 4> : S == 5 ? (const void*)k_split<1, 5>
+                                                                       : (const void*)k_split<1, 6>;
+    return S == 4 ? (const void*)k_split<2, 4> : S == 5 ? (const void*)k_split<2, 5> : (const void*)k_split<2, 6>;
+}
+
+tsm_status make_plan(int cplx, int M, int N, int64_t K, int S, Plan* pl) {
+    if (S < 4 || S > NSLICE_MAX) return TSM_ERR_NOT_SUPPORTED;
+    pl->S = S;
     const DeviceInfo& di = device_info();
     Params& prm = pl->prm;
     const int c = cplx ? 2 : 1;
@@ -871,9 +890,9 @@ tsm_status make_plan(int cplx, int M, int N, int64_t K, Plan* pl) {
     prm.Q = Q;
     prm.K = K;
     prm.stacked = P <= 64 ? 1 : 0;
-    // Y column chunks: one if 6 slices of it fit tensor memory, else two
-    // chunks split on an even column
-    if (Q <= 80) {
+    // Y column chunks: one if S slices of it fit tensor memory (512
+    // columns), else two chunks split on an even column
+    if (((Q + 15) & ~15) * S <= TMEM_COLS_MAX) {
         prm.n_qc = 1;
         prm.q0[0] = 0;
         prm.qw[0] = Q;
@@ -889,22 +908,22 @@ tsm_status make_plan(int cplx, int M, int N, int64_t K, Plan* pl) {
     }
     const int qmax = prm.qw[0] > prm.qw[1] ? prm.qw[0] : prm.qw[1];
     prm.Qp = (qmax + 15) & ~15;
-    if (count_mmas(prm.stacked, prm.Qp) > MAX_MMAS) return TSM_ERR_NOT_SUPPORTED;
+    if (count_mmas(prm.stacked, prm.Qp, S) > MAX_MMAS) return TSM_ERR_NOT_SUPPORTED;
 
-    // CTA shape.  Accumulators take 6 * Qp tensor-memory columns; the
+    // CTA shape.  Accumulators take S * Qp tensor-memory columns; the
     // allocation is the next power of two, so narrow chunks leave room for
     // several CTAs per SM, which then overlap one another's waits (drains,
     // load latency).  Shared memory is split between them and padded so that
     // no more CTAs than planned share an SM (a further one would block in its
     // tensor-memory allocation).
     int tcols = 32;
-    while (tcols < 6 * prm.Qp) tcols <<= 1;
+    while (tcols < S * prm.Qp) tcols <<= 1;
     prm.tmem_cols = tcols;
     const int units = 32 * ((((P + 7) & ~7) + qmax + 7) / 8);  // as make_layout
     pl->per = units <= Conv<1>::MAX_THREADS ? 1 : 2;
     prm.nconv = (((units + pl->per - 1) / pl->per) + 31) & ~31;
     if (prm.nconv > (pl->per == 1 ? Conv<1>::MAX_THREADS : Conv<2>::MAX_THREADS)) return TSM_ERR_NOT_SUPPORTED;
-    pl->fn = pl->per == 1 ? (const void*)k_split<1> : (const void*)k_split<2>;
+    pl->fn = kernel_for(pl->per, S);
     if (cudaFuncSetAttribute(pl->fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
         return TSM_ERR_LAUNCH;
     int cps_max = TMEM_COLS_MAX / tcols;
@@ -931,7 +950,7 @@ tsm_status make_plan(int cplx, int M, int N, int64_t K, Plan* pl) {
         const int thr = prm.nconv + (1 + nepi) * 32;
         const uint32_t budget = cc == 1 ? kSmemBudget : ((kSmemPerSM / cc - 1024u) & ~127u);
         const uint32_t floor_b = kSmemPerSM / (cc + 1);
-        const Layout L = make_layout(P, prm.Qp, qmax, prm.stacked, budget, floor_b);
+        const Layout L = make_layout(P, prm.Qp, qmax, prm.stacked, budget, floor_b, S);
         if (L.ndig < (cc > 1 ? 3 : 2) || L.total > (uint32_t)di.smem_optin) continue;
         if (fits(thr, L.total) == cc) {
             pl->cps = cc;
@@ -963,12 +982,16 @@ tsm_status make_plan(int cplx, int M, int N, int64_t K, Plan* pl) {
 }  // namespace split
 }  // namespace tsm
 
-extern "C" tsm_status tsm_tsmttsm_split(tsm_op opA, tsm_dtype dtype, int M, int N, int64_t K,
-                                        const double* alpha, const void* A, int64_t lda, const void* B,
-                                        int64_t ldb, const double* beta, void* C, int64_t ldc,
-                                        tsm_stream_t stream) {
+namespace tsm {
+namespace split {
+
+tsm_status run(tsm_op opA, tsm_dtype dtype, int M, int N, int64_t K, const double* alpha, const void* A,
+               int64_t lda, const void* B, int64_t ldb, const double* beta, void* C, int64_t ldc, int kind,
+               int slices, tsm_stream_t stream) {
     tsm_status st = validate_common(dtype, M, N, K, alpha, beta);
     if (st != TSM_OK) return st;
+    if (kind != TSM_SPLIT_DIGITS_F16) return TSM_ERR_INVALID_VALUE;
+    if (slices < 4 || slices > NSLICE_MAX) return TSM_ERR_NOT_SUPPORTED;
     if (opA != TSM_OP_T && opA != TSM_OP_C) return TSM_ERR_INVALID_VALUE;
     if (lda < M || ldb < N || ldc < N || !C) return TSM_ERR_INVALID_VALUE;
     const int cplx = dtype == TSM_C64;
@@ -986,15 +1009,15 @@ extern "C" tsm_status tsm_tsmttsm_split(tsm_op opA, tsm_dtype dtype, int M, int 
                    ? TSM_OK
                    : TSM_ERR_LAUNCH;
     }
-    split::Plan pl;
-    if ((st = split::make_plan(cplx, M, N, K, &pl)) != TSM_OK) return st;
-    split::Params& prm = pl.prm;
+    Plan pl;
+    if ((st = make_plan(cplx, M, N, K, slices, &pl)) != TSM_OK) return st;
+    Params& prm = pl.prm;
     const int c = cplx ? 2 : 1;
     prm.X = (const double*)A;
     prm.ldx = lda * c;
     prm.Y = (const double*)B;
     prm.ldy = ldb * c;
-    prm.timeout = split::g_timeout;
+    prm.timeout = g_timeout;
     const int n_kr = prm.n_kr, P = prm.P, Q = prm.Q;
 
     Workspace* ws = nullptr;
@@ -1005,28 +1028,45 @@ extern "C" tsm_status tsm_tsmttsm_split(tsm_op opA, tsm_dtype dtype, int M, int 
     prm.flush = ws->partials + (size_t)n_kr * P * Q;
     prm.err = reinterpret_cast<int*>(ws->tickets) + 32;  // error word of this stream
     if (cudaMemsetAsync(prm.err, 0, sizeof(int), s) != cudaSuccess) return TSM_ERR_LAUNCH;
-    if (pl.per == 1)
-        split::k_split<1><<<n_kr * prm.n_qc, pl.threads, pl.L.total, s>>>(prm);
-    else
-        split::k_split<2><<<n_kr * prm.n_qc, pl.threads, pl.L.total, s>>>(prm);
-    if (cudaGetLastError() != cudaSuccess) return TSM_ERR_LAUNCH;
+    void* args[] = {&prm};
+    if (cudaLaunchKernel(pl.fn, dim3(n_kr * prm.n_qc), dim3(pl.threads), args, pl.L.total, s) != cudaSuccess)
+        return TSM_ERR_LAUNCH;
     const int outs = M * N;
-    split::k_split_combine<<<(outs + 127) / 128, 128, 0, s>>>(
+    k_split_combine<<<(outs + 127) / 128, 128, 0, s>>>(
         ws->partials, n_kr, P, Q, M, N, cplx, (cplx && opA == TSM_OP_C) ? 1 : 0, alpha[0], cplx ? alpha[1] : 0.0,
         beta[0], cplx ? beta[1] : 0.0, beta_zero, (double*)C, ldc, prm.err);
     if (cudaGetLastError() != cudaSuccess) return TSM_ERR_LAUNCH;
     return TSM_OK;
 }
 
-extern "C" tsm_status tsm_split_plan(tsm_dtype dtype, int M, int N, int64_t K, tsm_split_plan_info* info) {
+}  // namespace split
+}  // namespace tsm
+
+extern "C" tsm_status tsm_tsmttsm_split(tsm_op opA, tsm_dtype dtype, int M, int N, int64_t K,
+                                        const double* alpha, const void* A, int64_t lda, const void* B,
+                                        int64_t ldb, const double* beta, void* C, int64_t ldc,
+                                        tsm_stream_t stream) {
+    return split::run(opA, dtype, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, TSM_SPLIT_DIGITS_F16, 6, stream);
+}
+
+extern "C" tsm_status tsm_tsmttsm_split_ex(tsm_op opA, tsm_dtype dtype, int M, int N, int64_t K,
+                                           const double* alpha, const void* A, int64_t lda, const void* B,
+                                           int64_t ldb, const double* beta, void* C, int64_t ldc,
+                                           tsm_split_kind kind, int slices, tsm_stream_t stream) {
+    return split::run(opA, dtype, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kind, slices, stream);
+}
+
+extern "C" tsm_status tsm_split_plan_ex(tsm_dtype dtype, int M, int N, int64_t K, int slices,
+                                        tsm_split_plan_info* info) {
     if (!info || (dtype != TSM_R64 && dtype != TSM_C64) || K < 1) return TSM_ERR_INVALID_VALUE;
-    if (M < 1 || N < 1 || M > 64 || N > 64) return TSM_ERR_NOT_SUPPORTED;
+    if (M < 1 || N < 1 || M > 64 || N > 64 || slices < 4 || slices > split::NSLICE_MAX)
+        return TSM_ERR_NOT_SUPPORTED;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return TSM_ERR_NO_DEVICE;
     const DeviceInfo& di = device_info();
     if (di.cc_major != 10 || di.cc_minor != 3) return TSM_ERR_NO_DEVICE;
     split::Plan pl;
-    const tsm_status st = split::make_plan(dtype == TSM_C64, M, N, K, &pl);
+    const tsm_status st = split::make_plan(dtype == TSM_C64, M, N, K, slices, &pl);
     if (st != TSM_OK) return st;
     info->ctas = pl.prm.n_kr * pl.prm.n_qc;
     info->ctas_per_sm = pl.cps;
@@ -1038,6 +1078,10 @@ extern "C" tsm_status tsm_split_plan(tsm_dtype dtype, int M, int N, int64_t K, t
     info->tmem_columns = pl.prm.tmem_cols;
     info->smem_bytes = (int)pl.L.total;
     return TSM_OK;
+}
+
+extern "C" tsm_status tsm_split_plan(tsm_dtype dtype, int M, int N, int64_t K, tsm_split_plan_info* info) {
+    return tsm_split_plan_ex(dtype, M, N, K, 6, info);
 }
 
 extern "C" tsm_status tsm_split_status(tsm_stream_t stream) {

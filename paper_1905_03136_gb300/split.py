@@ -18,6 +18,13 @@ _lib.extend_signatures({
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_int64,
                                          ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "tsm_tsmttsm_split_ex": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                            ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_int64,
+                                            ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_void_p]),
+    "tsm_split_plan_ex": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
+                                         ctypes.POINTER(PlanInfo)]),
     "tsm_split_status": (ctypes.c_int, [ctypes.c_void_p]),
     "tsm_split_set_timeout": (ctypes.c_int, [ctypes.c_int64]),
 })
@@ -25,8 +32,12 @@ _lib.extend_signatures({
 _OPS = {"T": 1, "C": 2}
 
 
-def tsmttsm_split(A, B, C=None, alpha=1.0, beta=0.0, op="T", stream=None):
-    """C = alpha * op(A)^T B + beta * C with the tensor-core split path."""
+DIGITS_F16 = 0
+
+
+def tsmttsm_split(A, B, C=None, alpha=1.0, beta=0.0, op="T", stream=None, slices=6, kind=DIGITS_F16):
+    """C = alpha * op(A)^T B + beta * C with the tensor-core split path
+    (`slices` 8-bit slices per input, 4..6)."""
     import torch
     from . import _dtype_code, _ld, _stream
     dt = _dtype_code(A)
@@ -36,9 +47,9 @@ def tsmttsm_split(A, B, C=None, alpha=1.0, beta=0.0, op="T", stream=None):
         C = torch.zeros((M, N), dtype=A.dtype, device=A.device)
         beta = 0.0
     cplx = dt == 1
-    _lib.call("tsm_tsmttsm_split", _OPS[op], dt, M, N, K, scalar(alpha, cplx), ctypes.c_void_p(A.data_ptr()),
+    _lib.call("tsm_tsmttsm_split_ex", _OPS[op], dt, M, N, K, scalar(alpha, cplx), ctypes.c_void_p(A.data_ptr()),
               _ld(A, "A"), ctypes.c_void_p(B.data_ptr()), _ld(B, "B"), scalar(beta, cplx),
-              ctypes.c_void_p(C.data_ptr()), _ld(C, "C"), _stream(stream))
+              ctypes.c_void_p(C.data_ptr()), _ld(C, "C"), int(kind), int(slices), _stream(stream))
     return C
 
 
@@ -52,9 +63,9 @@ def set_timeout(cycles):
     _lib.call("tsm_split_set_timeout", int(cycles))
 
 
-def plan(dtype, M, N, K):
-    """The launch plan (dict) tsm_tsmttsm_split would use for a shape;
+def plan(dtype, M, N, K, slices=6):
+    """The launch plan (dict) tsm_tsmttsm_split(_ex) would use for a shape;
     dtype is 0 (real) or 1 (complex)."""
     info = PlanInfo()
-    _lib.call("tsm_split_plan", int(dtype), int(M), int(N), int(K), ctypes.byref(info))
+    _lib.call("tsm_split_plan_ex", int(dtype), int(M), int(N), int(K), int(slices), ctypes.byref(info))
     return {n: getattr(info, n) for n, _ in PlanInfo._fields_}

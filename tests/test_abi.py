@@ -169,6 +169,20 @@ def test_argument_validation_without_device(lib):
     assert lib.tsm_tsmm(0, 0, 4, 4, 10, one, ctypes.c_void_p(1), 4, ctypes.c_void_p(1), 4, zero,
                         ctypes.c_void_p(0), 4, None) == INVALID
     assert lib.tsm_fill_random(ctypes.c_void_p(1), 0, 4, 4, 0, 0, 9, None) == INVALID
+    # split path precision knobs: an unknown split kind is malformed, a slice
+    # count outside [4, 6] is valid but not implemented
+    from paper_1905_03136_gb300 import split  # noqa: F401  (registers the signatures)
+
+    def split_ex(kind, slices):
+        return lib.tsm_tsmttsm_split_ex(1, 0, 4, 4, 10, one, ctypes.c_void_p(1), 4, ctypes.c_void_p(1), 4, zero,
+                                        ctypes.c_void_p(1), 4, kind, slices, None)
+    assert split_ex(1, 6) == INVALID
+    assert split_ex(-1, 6) == INVALID
+    for bad in (0, 3, 7, 8):
+        assert split_ex(0, bad) == UNSUPPORTED, bad
+    info = split.PlanInfo()
+    for bad in (3, 7):
+        assert lib.tsm_split_plan_ex(0, 4, 4, 100, bad, ctypes.byref(info)) == UNSUPPORTED
 
 
 def test_no_device_is_an_error_not_a_fallback(lib):

@@ -69,6 +69,41 @@ def test_split_random_inputs(sp, case, dist):
         assert err <= TOL, (op, err)
 
 
+SLICE_SHAPES = [(False, 7, 5), (False, 64, 64), (False, 33, 17), (True, 8, 8), (True, 32, 32), (True, 48, 48),
+                (True, 64, 64), (True, 33, 41)]
+
+
+@pytest.mark.parametrize("slices", [4, 5, 6])
+@pytest.mark.parametrize("case", SLICE_SHAPES, ids=lambda c: "%s_%dx%d" % ("c64" if c[0] else "r64", c[1], c[2]))
+def test_split_slice_count(sp, case, slices):
+    """Each slice count S keeps 8S - 1 bits per input: small integers stay
+    exact (bit for bit), uniform inputs meet a normwise bound of
+    32 * 2^-(8S-1) against the oracle (S = 6: the 1e-12 bar with room), and
+    the default call is S = 6 bit for bit."""
+    cplx, M, N = case
+    K = 4099
+    op = "C" if cplx else "T"
+    Ai = synth.block_vector(5, K, M, complex_=cplx, dist="smallint")
+    Bi = synth.block_vector(6, K, N, complex_=cplx, dist="smallint")
+    got = host(sp.tsmttsm_split(dev(Ai), dev(Bi), op=op, slices=slices))
+    assert np.array_equal(got, oracle.gram(Ai, Bi, op))
+    A = synth.block_vector(7, K, M, complex_=cplx)
+    B = synth.block_vector(8, K, N, complex_=cplx)
+    dA, dB = dev(A), dev(B)
+    got = host(sp.tsmttsm_split(dA, dB, op=op, slices=slices))
+    err = oracle.rel_fro(got, oracle.gram(A, B, op))
+    assert err <= 32 * 2.0 ** -(8 * slices - 1), (slices, err)
+    if slices == 6:
+        assert err <= TOL
+        assert np.array_equal(got, host(sp.tsmttsm_split(dA, dB, op=op)))
+    else:
+        # fewer slices: never more accurate than the full split
+        assert err >= oracle.rel_fro(host(sp.tsmttsm_split(dA, dB, op=op)), oracle.gram(A, B, op))
+    pl = sp.plan(int(cplx), M, N, K, slices)
+    assert pl["tmem_columns"] <= 512
+    assert sp.status() == 0
+
+
 def test_split_alpha_beta_ld_nan_and_k0(sp):
     M, N, K = 24, 40, 30011
     lda, ldb, ldc = M + 3, N + 5, N + 2
