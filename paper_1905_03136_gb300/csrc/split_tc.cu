@@ -891,8 +891,10 @@ tsm_status make_plan(int cplx, int M, int N, int64_t K, int S, Plan* pl) {
     prm.K = K;
     prm.stacked = P <= 64 ? 1 : 0;
     // Y column chunks: one if S slices of it fit tensor memory (512
-    // columns), else two chunks split on an even column
-    if (((Q + 15) & ~15) * S <= TMEM_COLS_MAX) {
+    // columns) and its conversion units fit the converter warps (two per
+    // thread at most), else two chunks split on an even column
+    const int units_one = 32 * ((((P + 7) & ~7) + Q + 7) / 8);
+    if (((Q + 15) & ~15) * S <= TMEM_COLS_MAX && units_one <= 2 * Conv<2>::MAX_THREADS) {
         prm.n_qc = 1;
         prm.q0[0] = 0;
         prm.qw[0] = Q;
