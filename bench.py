@@ -794,6 +794,38 @@ def run_widths_extra(flatA, flatB, K, bw, p64):
     return res
 
 
+GRID_STEP = 8
+
+
+def run_grid_extra(flatA, flatB, K, bw, p64):
+    """Non-square widths: TSMTTSM at every (M, N) with M, N multiples of 8 in
+    8..64 (real op T and complex op C) at K = 2^24, percent of roofline per
+    shape with the library's tuned choice; one warm-up and one timed call."""
+    import torch
+    import paper_1905_03136_gb300 as tsm
+    res = {}
+    below = []
+    for cplx in (False, True):
+        dt = torch.complex128 if cplx else torch.float64
+        pct = []
+        for M in range(GRID_STEP, 65, GRID_STEP):
+            row = []
+            for N in range(GRID_STEP, 65, GRID_STEP):
+                A, B = _views(flatA, flatB, cplx, M, N, K)
+                C = torch.zeros((M, N), dtype=dt, device=flatA.device)
+                ms = _time(lambda: tsm.tsmttsm(A, B, C, op="C" if cplx else "T"), reps=1)
+                p = 100.0 * ideal_seconds(cplx, M, N, K, bw, p64) / (ms * 1e-3)
+                row.append(round(p, 1))
+                if p < 90.0:
+                    below.append("%s %dx%d: %.1f" % ("c64" if cplx else "r64", M, N, p))
+            pct.append(row)
+        flat = [x for r in pct for x in r]
+        res["c64" if cplx else "r64"] = {"roofline_pct": pct, "median": statistics.median(flat), "min": min(flat)}
+    res["what"] = "TSMTTSM % of roofline, rows M = 8, 16, ..., 64, columns N = 8, 16, ..., 64, K = 2^24"
+    res["below_90"] = below
+    return res
+
+
 GS_CASES = [(True, 32, 32), (True, 64, 64), (False, 64, 64), (False, 8, 8)]
 
 
@@ -1022,6 +1054,10 @@ def run_extras(args, flatA, flatB, K, bw, p64, emit):
                                       [i + 1 for i, p in enumerate(w[kind][dt]["roofline_pct"]) if p < 90.0]]
                                  for dt in ("r64", "c64")} for kind in ("tsmttsm", "tsmm_beta0", "tsmm_beta1")}
         summ["widths"]["what"] = "M=N=w, w=1..64: [median %, min %, widths below 90 %]"
+    g = guarded("grid", lambda: run_grid_extra(flatA, flatB, K, bw, p64))
+    if "error" not in g:
+        summ["grid_8"] = {dt: [g[dt]["median"], g[dt]["min"]] for dt in ("r64", "c64")}
+        summ["grid_8"]["below_90"] = len(g["below_90"])
     sp = guarded("split", lambda: run_split_extra(flatA, flatB, K, bw))
     if isinstance(sp, list):
         summ["split"] = {"%s %dx%d %s" % (r["dtype"], r["M"], r["N"], r["dist"][:4]):

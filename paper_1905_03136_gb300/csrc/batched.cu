@@ -443,7 +443,7 @@ __device__ void run_tsmm(const Inst& in, const Item& it, double* cs) {
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_batched(const Inst* __restrict__ insts,
+__global__ void __launch_bounds__(kThreads, 2) k_batched(const Inst* __restrict__ insts,
                                                       const Item* __restrict__ items, int n_items,
                                                       unsigned* counter, unsigned* tickets, double* parts) {
     extern __shared__ double dyn[];
