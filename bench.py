@@ -854,10 +854,29 @@ def run_gs_extra(flatA, flatB, K, bw, p64):
         meas += ms * 1e-3
         out.append({"dtype": "c64" if cplx else "r64", "M": M, "N": N, "ms": round(ms, 4),
                     "roofline_pct": round(100 * t_ideal / (ms * 1e-3), 2)})
+    # small K: the step against its two products timed alone (the gap is
+    # what a single fused kernel could remove at most: one launch and the C
+    # round trip through L2)
+    small = []
+    for (cplx, M, N) in ((True, 32, 32), (False, 8, 8)):
+        c = 2 if cplx else 1
+        for Ks in (10 ** 4, 10 ** 5, 10 ** 6):
+            A = flatA[: Ks * M * c]
+            B = Bw[: Ks * N * c]
+            B.copy_(flatB[: Ks * N * c])
+            if cplx:
+                A, B = A.view(torch.complex128), B.view(torch.complex128)
+            A, B = A.view(Ks, M), B.view(Ks, N)
+            C = torch.empty((M, N), dtype=A.dtype, device=A.device)
+            t_gs = _time(lambda: tsm.gs_step(A, B, C), reps=50, warm=5)
+            t_1 = _time(lambda: tsm.tsmttsm(A, B, C, op="C"), reps=50, warm=5)
+            t_2 = _time(lambda: tsm.tsmm(A, C, B, -1.0, 1.0), reps=50, warm=5)
+            small.append({"dtype": "c64" if cplx else "r64", "M": M, "N": N, "K": Ks, "gs_us": round(t_gs * 1e3, 2),
+                          "tsmttsm_us": round(t_1 * 1e3, 2), "tsmm_us": round(t_2 * 1e3, 2)})
     del Bw
     torch.cuda.empty_cache()
     return {"what": "tsm_gs_step: TSMTTSM (op C) then TSMM (alpha=-1, beta=1) on one stream, C on the device",
-            "roofline_pct_all": 100 * ideal / meas, "calls": out}
+            "roofline_pct_all": 100 * ideal / meas, "calls": out, "small_k": small}
 
 
 RAMP_K = [10 ** 4, 3 * 10 ** 4, 10 ** 5, 3 * 10 ** 5, 10 ** 6, 1 << 21, 1 << 22, 1 << 24]

@@ -3,7 +3,8 @@
 // G = X^T Y for real tall & skinny X (K x P) and Y (K x Q) in binary64 --
 // complex A^T B / A^H B are the real product of the interleaved (re, im)
 // columns, recombined at the end -- computed with error-free splitting after
-// Ozaki, Ogita, Oishi, Rump (Numer. Algorithms 59, 2012):
+// Ozaki, Ogita, Oishi, Rump (Numer. Algorithms 59, 2012), shown here for
+// S = 6 slices (the kernel is templated on S in [4, 6]):
 //
 //   x = 2^e * sum_s alpha_s * 2^(-7 - 8s),  s = 0..5, alpha_s integer, |alpha_s| <= 128
 //
@@ -26,15 +27,15 @@
 // CTA organisation (one to four CTAs per SM, as tensor memory and shared
 // memory allow; each persistent over a contiguous K range and a chunk of Y's
 // columns):
-//   converter warps  each thread owns one or two fixed "units" (4 rows of
-//                    one column in every 16-row step) and keeps the global
-//                    loads of its next one or two steps in flight in
-//                    registers (the paper's leap frogging, Sec. 3.1, made
-//                    deep); it keeps its columns' running exponents in
-//                    registers and writes the six fp16 slices of its values
-//                    into a ring of digit stages in the canonical K-major
-//                    core-matrix layout of the MMA operands.  The warps do
-//                    not synchronise with one another: a warp whose column
+//   converter warps  each thread owns one fixed "unit" (8 rows of one
+//                    column in every 16-row step) and keeps the global
+//                    loads of its next step in flight in registers (the
+//                    paper's leap frogging, Sec. 3.1); it keeps its column's
+//                    running exponent in a register and writes the S fp16
+//                    slices of its 8 values, 16 bytes per slice, into a ring
+//                    of digit stages in the canonical K-major core-matrix
+//                    layout of the MMA operands.  The warps do not
+//                    synchronise with one another: a warp whose column
 //                    exponent grew stamps the stage with the step index;
 //   MMA warp         allocates tensor memory; lane 0 issues tcgen05.mma and
 //                    decides the tile boundaries (a stamped stage, or 16
@@ -77,22 +78,29 @@ constexpr int TMEM_COLS_MAX = 512;
 constexpr int E_NONE = -4000;       // running exponent before any nonzero value
 constexpr long long kDefaultTimeout = 4000000000ll;  // SM cycles (~2 s)
 
-// Converter configurations: PER units per thread, DEPTH steps of loads in
-// flight ahead of the step being converted (DEPTH + 1 register sets).
-template <int PER>
+// Converter configuration: each converter thread owns one unit of R rows
+// (4 or 8) of one column in every 16-row step, with the loads of DEPTH
+// further steps in flight (DEPTH + 1 register sets).  R = 4 gives four
+// units per column (more threads, for products of at most 128 columns);
+// R = 8 gives two, stored as whole 16-byte core-matrix rows (wider
+// products, up to 208 columns P + Qw per CTA).  The CTA size bounds the
+// registers per thread.
+template <int R>
 struct Conv;
 template <>
-struct Conv<1> {
+struct Conv<4> {
     static constexpr int MAX_THREADS = 512, DEPTH = 2;
 };
 template <>
-struct Conv<2> {
+struct Conv<8> {
     static constexpr int MAX_THREADS = 416, DEPTH = 1;
 };
-template <int PER>
+template <int R>
 constexpr int block_threads() {
-    return Conv<PER>::MAX_THREADS + (1 + NEPI_MAX) * 32;
+    return Conv<R>::MAX_THREADS + (1 + NEPI_MAX) * 32;
 }
+// converter threads a CTA needs for `cols` columns with R-row units
+__host__ __device__ constexpr int conv_threads(int cols, int R) { return 32 * (((16 / R) * cols + 31) / 32); }
 
 struct Params {
     const double* X;
@@ -214,7 +222,6 @@ __device__ __forceinline__ bool elect_one() {
 
 struct Layout {
     int nrb;            // 128-row blocks of operand A per step
-    int units;          // (column slot, 4-row group) units per step, a multiple of 32
     int ndig;           // digit stages
     int ne;             // exponent entries: P + Qp
     uint32_t a_bytes;   // operand A bytes per step
@@ -236,7 +243,6 @@ __host__ __device__ inline Layout make_layout(int P, int Qp, int Qw, int stacked
                                               uint32_t floor_bytes, int S) {
     Layout L;
     L.nrb = stacked ? (S + 1) / 2 : S;
-    L.units = 32 * ((((P + 7) & ~7) + Qw + 7) / 8);  // 4 units per column slot, 8 slots per group of 32
     L.ne = P + Qp;
     L.a_bytes = (uint32_t)L.nrb * 4096u;
     L.b_bytes = (uint32_t)S * Qp * 32u;
@@ -295,6 +301,23 @@ __device__ __forceinline__ unsigned long long fixed_digits(double x, int e, uint
     return (mant >> sh) + kBias;
 }
 
+// fixed_digits for columns whose running exponent e exceeds -960, with the
+// shift base Eb = e + 1076 - 8S precomputed per column: the implicit bit is
+// set unconditionally, which changes nothing here, since a zero or
+// subnormal x (exponent field 0) then shifts by at least 63 and gives 0, as
+// its exact value (|x| < 2^-1022, so |x| 2^(8S-1-e) < 2^-15) does.
+template <int S>
+__device__ __forceinline__ unsigned long long fixed_digits_fast(double x, int Eb, uint32_t* sign) {
+    constexpr unsigned long long kBias = ((1ull << (8 * (S - 1))) - 1) / 255 * 0x80;
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const uint32_t hi = (uint32_t)(bits >> 32);
+    *sign = hi & 0x80000000u;
+    const int ef = (int)((hi >> 20) & 0x7FFu);
+    const uint32_t mhi = (hi & 0xFFFFFu) | 0x100000u;
+    const unsigned long long mant = ((unsigned long long)mhi << 32) | (uint32_t)bits;
+    return (mant >> min(Eb - ef, 63)) + kBias;
+}
+
 // The S fp16 slices of two values a (row r) and b (row r + 1) of one
 // column, packed per slice as (a, b) in one 32-bit word, sign applied.  A
 // digit byte placed under the fp16 exponent of 1024 (0x64XX) is 1024 + byte
@@ -303,10 +326,12 @@ __device__ __forceinline__ unsigned long long fixed_digits(double x, int e, uint
 // sign * (1024 + byte) - sign * bias, bias = 1024 for the top digit and 1152
 // (1024 + 128) for the balanced low digits: exact, since every result is a
 // small integer.  Slice s is byte S - 1 - s of Y.
-template <int S>
+// FAST: `e` is the shift base of fixed_digits_fast instead of the exponent.
+template <int S, bool FAST>
 __device__ __forceinline__ void split_pair(double xa, double xb, int e, uint32_t* w) {
     uint32_t sa, sb;
-    const unsigned long long ya = fixed_digits<S>(xa, e, &sa), yb = fixed_digits<S>(xb, e, &sb);
+    const unsigned long long ya = FAST ? fixed_digits_fast<S>(xa, e, &sa) : fixed_digits<S>(xa, e, &sa);
+    const unsigned long long yb = FAST ? fixed_digits_fast<S>(xb, e, &sb) : fixed_digits<S>(xb, e, &sb);
     const uint32_t alo = (uint32_t)ya, ahi = (uint32_t)(ya >> 32);
     const uint32_t blo = (uint32_t)yb, bhi = (uint32_t)(yb >> 32);
     const uint32_t sg = (sa >> 16) | sb;       // sign of a in bit 15, of b in bit 31
@@ -371,9 +396,10 @@ __device__ __forceinline__ uint32_t kmajor_off(int r, int g) {
 
 // ------------------------------------------------------------ the kernel
 
-template <int PER, int S>
-__global__ void __launch_bounds__(block_threads<PER>(), 1) k_split(const Params prm) {
-    constexpr int DEPTH = Conv<PER>::DEPTH;
+template <int R, int S>
+__global__ void __launch_bounds__(block_threads<R>(), 1) k_split(const Params prm) {
+    constexpr int PER = 1;  // units per converter thread
+    constexpr int DEPTH = Conv<R>::DEPTH;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int P = prm.P;
     const int kr = blockIdx.x / prm.n_qc, qc = blockIdx.x - kr * prm.n_qc;
@@ -440,17 +466,18 @@ __global__ void __launch_bounds__(block_threads<PER>(), 1) k_split(const Params 
 
     if (warp < NCONV_WARPS) {
         // ================================================= converters
-        // Unit u = threadIdx.x + i * NCONV (i < PER) of every step.  Each
-        // group of 32 units covers 8 column slots: slot c = 8 (u / 32) +
-        // (u / 2) % 8, k-group g = (u / 16) % 2 of the K-major core rows
-        // (rows 8g .. 8g + 7 of the step), byte offset 8 (u % 2) inside them
-        // (rows 8g + 4 (u % 2) .. + 3).  A half-warp thus stores one
-        // contiguous 128-byte core row (no bank conflicts), and the four
-        // units of a column are lanes l, l ^ 1, l ^ 16, l ^ 17.  Slots
-        // [0, P) are X's columns, [P8, P8 + Qw) this chunk's Y columns
-        // (P8 = P rounded up to 8, so Y starts on a group); the rest are idle.
+        // Unit u = threadIdx.x of every step.  R = 8: rows 8g .. 8g + 7 of
+        // the step (g = (u / 16) % 2) of column slot c = 16 (u / 32) + u % 16;
+        // its 8 digits of one slice are the 16 contiguous bytes of one
+        // K-major core-matrix row, written with a single 16-byte store, and
+        // a warp's store covers 512 contiguous bytes (four core matrices);
+        // the two units of a column are lanes l and l ^ 16.  R = 4: rows
+        // 8g + 4h .. + 3 (h = u % 2) of slot c = 8 (u / 32) + (u / 2) % 8,
+        // 8-byte stores, a half-warp writing one 128-byte core row; the four
+        // units of a column are lanes l, l ^ 1, l ^ 16, l ^ 17.  No bank
+        // conflicts either way.  Slots [0, P) are X's columns, [P, P + Qw)
+        // this chunk's Y columns; the rest are idle.
         const int ct = threadIdx.x;
-        const int P8 = (P + 7) & ~7;
         bool valid[PER];
         const char* src[PER];   // column base
         int64_t ldb[PER];       // row stride in bytes
@@ -462,12 +489,13 @@ __global__ void __launch_bounds__(block_threads<PER>(), 1) k_split(const Params 
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
             const int u = ct + i * NCONV;
-            const int slot = 8 * (u >> 5) + ((u >> 1) & 7), g = (u >> 4) & 1, hb = u & 1;
-            const bool is_x = slot < P, is_y = slot >= P8 && slot < P8 + Qw;
+            const int slot = R == 8 ? 16 * (u >> 5) + (u & 15) : 8 * (u >> 5) + ((u >> 1) & 7);
+            const int g = (u >> 4) & 1, hb = R == 8 ? 0 : (u & 1);
+            const bool is_x = slot < P, is_y = slot >= P && slot < P + Qw;
             valid[i] = is_x || is_y;
-            const int c = is_x ? slot : (is_y ? P + (slot - P8) : 0);  // X columns, then Y columns
+            const int c = valid[i] ? slot : 0;  // X columns, then Y columns
             rq[i] = 8 * g + 4 * hb;
-            owner[i] = valid[i] && (u & 0x11) == 0;
+            owner[i] = valid[i] && g == 0 && hb == 0;
             col[i] = c;
             e[i] = E_NONE;
             if (c < P) {
@@ -483,32 +511,39 @@ __global__ void __launch_bounds__(block_threads<PER>(), 1) k_split(const Params 
                 dsl[i] = (uint32_t)Qp * 32u;
             }
         }
-        // loads of step s (zero beyond this CTA's steps and beyond row K)
-        auto load_step = [&](double(&v)[PER][4], int64_t s) {
+        // loads of step s (zero beyond this CTA's steps and beyond row K);
+        // whole steps inside the matrix skip the per-row bounds checks
+        auto load_step = [&](double(&v)[PER][R], int64_t s) {
 #pragma unroll
             for (int i = 0; i < PER; ++i) {
                 const int64_t k = (s_begin + s) * KSTEP + rq[i];
                 const bool live = valid[i] && s < nsteps;
                 const int64_t left = live ? Ktot - k : 0;
                 const char* p = src[i] + (live ? k : 0) * ldb[i];
+                if (left >= R) {
 #pragma unroll
-                for (int r = 0; r < 4; ++r)
-                    v[i][r] = left > r ? __ldg(reinterpret_cast<const double*>(p + r * ldb[i])) : 0.0;
+                    for (int r = 0; r < R; ++r) v[i][r] = __ldg(reinterpret_cast<const double*>(p + r * ldb[i]));
+                } else {
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        v[i][r] = left > r ? __ldg(reinterpret_cast<const double*>(p + r * ldb[i])) : 0.0;
+                }
             }
         };
         int d = 0;
         uint32_t phase = 0;
+        bool fast = false;  // every valid column's exponent above -960 (set when one grows)
         // converts step s from registers into digit stage d; false: stop
-        auto convert_step = [&](const double(&v)[PER][4], int64_t s) -> bool {
-            // -- running column exponents (registers; the four lanes of a column agree)
+        auto convert_step = [&](const double(&v)[PER][R], int64_t s) -> bool {
+            // -- running column exponents (registers; the lanes of a column agree)
             bool grew = false;
 #pragma unroll
             for (int i = 0; i < PER; ++i) {
                 uint32_t hm = 0;
 #pragma unroll
-                for (int r = 0; r < 4; ++r)
+                for (int r = 0; r < R; ++r)
                     hm = max(hm, (uint32_t)((unsigned long long)__double_as_longlong(v[i][r]) >> 32) & 0x7FFFFFFFu);
-                hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, 1));
+                if (R == 4) hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, 1));
                 hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, 16));
                 const int em = exp_from_hi(hm);
                 if (valid[i] && em > e[i]) {
@@ -517,6 +552,12 @@ __global__ void __launch_bounds__(block_threads<PER>(), 1) k_split(const Params 
                 }
             }
             grew = __any_sync(0xffffffffu, grew);
+            if (grew) {
+                bool tiny = false;
+#pragma unroll
+                for (int i = 0; i < PER; ++i) tiny |= valid[i] && e[i] <= -960;
+                fast = !__any_sync(0xffffffffu, tiny);
+            }
             // -- the stage must be free (waited by lane 0, broadcast: warp-uniform)
             int w_ok = 1;
             if (lane == 0)
@@ -532,17 +573,33 @@ __global__ void __launch_bounds__(block_threads<PER>(), 1) k_split(const Params 
             for (int i = 0; i < PER; ++i) {
                 if (!valid[i]) continue;
                 if (owner[i]) ex[col[i]] = e[i];
-                uint32_t w[S][2];
+                uint32_t w[S][R / 2];
+                if (fast) {  // warp-uniform
+                    const int eb = e[i] + 1076 - 8 * S;
 #pragma unroll
-                for (int r = 0; r < 4; r += 2) {
-                    uint32_t wp[S];
-                    split_pair<S>(v[i][r], v[i][r + 1], e[i], wp);
+                    for (int r = 0; r < R; r += 2) {
+                        uint32_t wp[S];
+                        split_pair<S, true>(v[i][r], v[i][r + 1], eb, wp);
 #pragma unroll
-                    for (int sl = 0; sl < S; ++sl) w[sl][r >> 1] = wp[sl];
+                        for (int sl = 0; sl < S; ++sl) w[sl][r >> 1] = wp[sl];
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < R; r += 2) {
+                        uint32_t wp[S];
+                        split_pair<S, false>(v[i][r], v[i][r + 1], e[i], wp);
+#pragma unroll
+                        for (int sl = 0; sl < S; ++sl) w[sl][r >> 1] = wp[sl];
+                    }
                 }
 #pragma unroll
-                for (int sl = 0; sl < S; ++sl)
-                    *reinterpret_cast<uint2*>(stage + off0[i] + sl * dsl[i]) = make_uint2(w[sl][0], w[sl][1]);
+                for (int sl = 0; sl < S; ++sl) {
+                    if (R == 8)
+                        *reinterpret_cast<uint4*>(stage + off0[i] + sl * dsl[i]) =
+                            make_uint4(w[sl][0], w[sl][1], w[sl][R == 8 ? 2 : 0], w[sl][R == 8 ? 3 : 1]);
+                    else
+                        *reinterpret_cast<uint2*>(stage + off0[i] + sl * dsl[i]) = make_uint2(w[sl][0], w[sl][1]);
+                }
             }
             fence_proxy_async();
             __syncwarp();
@@ -555,7 +612,7 @@ __global__ void __launch_bounds__(block_threads<PER>(), 1) k_split(const Params 
         };
         // DEPTH + 1 register sets in rotation: while step s is converted,
         // the loads of steps s + 1 .. s + DEPTH are in flight
-        double buf[DEPTH + 1][PER][4];
+        double buf[DEPTH + 1][PER][R];
 #pragma unroll
         for (int j = 0; j < DEPTH; ++j) load_step(buf[j], j);
         bool alive = true;
@@ -866,17 +923,17 @@ struct Plan {
     Params prm;     // shape fields filled; pointers, workspace and timeout are the caller's
     Layout L;
     int S = 6;      // slices per input
-    int per = 1;    // converter units per thread
+    int per = 8;    // rows per converter unit (R)
     int cps = 0;    // CTAs per SM
     int threads = 0;
     const void* fn = nullptr;
 };
 
 // The kernel instantiation for (units per thread, slices).
-const void* kernel_for(int per, int S) {
-    if (per == 1) return S == 4 ? (const void*)k_split<1, 4> : S == 5 ? (const void*)k_split<1, 5>
-                                                                       : (const void*)k_split<1, 6>;
-    return S == 4 ? (const void*)k_split<2, 4> : S == 5 ? (const void*)k_split<2, 5> : (const void*)k_split<2, 6>;
+const void* kernel_for(int R, int S) {
+    if (R == 4) return S == 4 ? (const void*)k_split<4, 4> : S == 5 ? (const void*)k_split<4, 5>
+                                                                     : (const void*)k_split<4, 6>;
+    return S == 4 ? (const void*)k_split<8, 4> : S == 5 ? (const void*)k_split<8, 5> : (const void*)k_split<8, 6>;
 }
 
 tsm_status make_plan(int cplx, int M, int N, int64_t K, int S, Plan* pl) {
@@ -891,10 +948,9 @@ tsm_status make_plan(int cplx, int M, int N, int64_t K, int S, Plan* pl) {
     prm.K = K;
     prm.stacked = P <= 64 ? 1 : 0;
     // Y column chunks: one if S slices of it fit tensor memory (512
-    // columns) and its conversion units fit the converter warps (two per
-    // thread at most), else two chunks split on an even column
-    const int units_one = 32 * ((((P + 7) & ~7) + Q + 7) / 8);
-    if (((Q + 15) & ~15) * S <= TMEM_COLS_MAX && units_one <= 2 * Conv<2>::MAX_THREADS) {
+    // columns) and its conversion units fit the converter warps, else two
+    // chunks split on an even column
+    if (((Q + 15) & ~15) * S <= TMEM_COLS_MAX && conv_threads(P + Q, 8) <= Conv<8>::MAX_THREADS) {
         prm.n_qc = 1;
         prm.q0[0] = 0;
         prm.qw[0] = Q;
@@ -921,10 +977,10 @@ tsm_status make_plan(int cplx, int M, int N, int64_t K, int S, Plan* pl) {
     int tcols = 32;
     while (tcols < S * prm.Qp) tcols <<= 1;
     prm.tmem_cols = tcols;
-    const int units = 32 * ((((P + 7) & ~7) + qmax + 7) / 8);  // as make_layout
-    pl->per = units <= Conv<1>::MAX_THREADS ? 1 : 2;
-    prm.nconv = (((units + pl->per - 1) / pl->per) + 31) & ~31;
-    if (prm.nconv > (pl->per == 1 ? Conv<1>::MAX_THREADS : Conv<2>::MAX_THREADS)) return TSM_ERR_NOT_SUPPORTED;
+    // unit rows: 4 (more converter threads) when they fit, else 8
+    pl->per = conv_threads(P + qmax, 4) <= Conv<4>::MAX_THREADS ? 4 : 8;
+    prm.nconv = conv_threads(P + qmax, pl->per);
+    if (prm.nconv > (pl->per == 4 ? Conv<4>::MAX_THREADS : Conv<8>::MAX_THREADS)) return TSM_ERR_NOT_SUPPORTED;
     pl->fn = kernel_for(pl->per, S);
     if (cudaFuncSetAttribute(pl->fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
         return TSM_ERR_LAUNCH;
