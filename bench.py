@@ -935,7 +935,7 @@ def batched_configs_from_model(insts, model):
     from paper_1905_03136_gb300 import costmodel as cm
     import paper_1905_03136_gb300 as tsm
     tiles = {1: (1, 1, 4), 2: (2, 2, 2), 3: (4, 4, 1), 4: (4, 8, 1), 5: (8, 4, 1), 6: (3, 3, 2), 7: (2, 5, 2),
-             8: (5, 2, 2), 9: (3, 5, 1), 10: (5, 3, 1), 11: (2, 7, 1), 12: (7, 2, 1)}
+             8: (5, 2, 2), 9: (3, 5, 1), 10: (5, 3, 1), 11: (2, 7, 1), 12: (7, 2, 1), 13: (8, 8, 1), 14: (5, 5, 1)}
     tprs = {1: 4, 2: 8, 3: 16}
     rt = {v["dtype"]: v["index"] for v in tsm.variants(tsm.KIND_TSMM) if v["name"].endswith("_rt_npt4_u2")}
     cfg = []
@@ -943,8 +943,8 @@ def batched_configs_from_model(insts, model):
         cands, feats = [], []
         if kind == 0:
             for code, (tm, tn, u) in tiles.items():
-                if cplx and code in (4, 5):
-                    tm, tn = 4, 4  # complex runs these codes with a 4x4 tile
+                if cplx and code in (4, 5, 13, 14):
+                    continue  # complex runs these codes as codes 3 and 6
                 if math.ceil(M / tm) * math.ceil(N / tn) > 256:
                     continue
                 cands.append(code)
@@ -964,16 +964,12 @@ def batched_configs_from_model(insts, model):
     return cfg
 
 
-def run_batched_extra(flatA, flatB):
-    """256 instances in one graph launch: default configurations vs the cost
-    model's, against launching every instance separately."""
+def batched_views(flatA, flatB, insts):
+    """Device views (A, B, out) of every batched instance: A and B read the
+    two seeded pools, every output has its own buffer."""
     import torch
-    from paper_1905_03136_gb300 import batched as bt
-    from paper_1905_03136_gb300 import costmodel as cm
-    import paper_1905_03136_gb300 as tsm
-    insts = batched_workload()
     dev = flatA.device
-    outs, views = [], []
+    views = []
     for (kind, cplx, M, N, K) in insts:
         c = 2 if cplx else 1
         dt = torch.complex128 if cplx else torch.float64
@@ -990,26 +986,97 @@ def run_batched_extra(flatA, flatB):
         B = B.view(K, N) if kind == 0 else B.view(M, N)
         O = O.view(M, N) if kind == 0 else O.view(K, N)
         views.append((A, B, O))
+    return views
+
+
+BATCHED_TILE_CODES = range(1, 15)
+BATCHED_TPR_CODES = range(1, 5)
+
+
+def batched_make(insts, views, cfgs):
+    from paper_1905_03136_gb300 import batched as bt
+    descs = [bt.desc(k, A, B, O, 1.0, 0.0, ("C" if c else "T") if k == 0 else "N", cfg)
+             for (k, c, M, N, K), (A, B, O), cfg in zip(insts, views, cfgs)]
+    return bt.Batch(descs)
+
+
+def batched_configs_exhaustive(insts, flatA, flatB, k_probe=1 << 19):
+    """Exhaustive per-instance configuration: for every distinct instance
+    shape (kind, dtype, M, N), each configuration code of the batched kernel
+    is timed on a one-shape batch of `k_probe` rows cut into 1024-row items
+    (enough items for every persistent CTA, so the time is the code's
+    throughput, not one item's latency); the fastest code is kept."""
+    best = {}
+    for inst in insts:
+        key = tuple(inst[:4])
+        if key in best:
+            continue
+        kind, cplx = key[0], key[1]
+        probe = key + (k_probe,)
+        v = batched_views(flatA, flatB, [probe])
+        times = {}
+        for code in (BATCHED_TILE_CODES if kind == 0 else BATCHED_TPR_CODES):
+            if kind == 0 and code_tile_threads(code, cplx, key[2], key[3]) > 256:
+                continue
+            b = batched_make([probe], v, [code | (10 << 8)])
+            times[code] = _time(b.run, reps=2)
+            b.close()
+        best[key] = min(times, key=times.get)
+        del v
+    return [best[tuple(i[:4])] for i in insts], len(best)
+
+
+def code_tile_threads(code, cplx, M, N):
+    """Threads per row lane of a batched TSMTTSM tile code (the kernel falls
+    back to its default for a code above 256)."""
+    tiles = {1: (1, 1), 2: (2, 2), 3: (4, 4), 4: (4, 8), 5: (8, 4), 6: (3, 3), 7: (2, 5), 8: (5, 2), 9: (3, 5),
+             10: (5, 3), 11: (2, 7), 12: (7, 2), 13: (8, 8), 14: (5, 5)}
+    tm, tn = tiles[code]
+    if cplx and code in (4, 5, 13):
+        tm = tn = 4
+    if cplx and code == 14:
+        tm = tn = 3
+    return math.ceil(M / tm) * math.ceil(N / tn)
+
+
+def run_batched_extra(flatA, flatB, exhaustive=True):
+    """256 instances in one graph launch: the default configurations, the cost
+    model's and the exhaustive per-instance best (every code timed per shape),
+    against launching every instance separately with the library's own
+    choices."""
+    import torch
+    from paper_1905_03136_gb300 import costmodel as cm
+    import paper_1905_03136_gb300 as tsm
+    insts = batched_workload()
+    views = batched_views(flatA, flatB, insts)
     flops = sum(2.0 * M * N * K * (4 if c else 1) for (_, c, M, N, K) in insts)
     res = {"instances": len(insts), "flops": flops}
 
-    def make(cfgs):
-        descs = [bt.desc(k, A, B, O, 1.0, 0.0, ("C" if c else "T") if k == 0 else "N", cfg)
-                 for (k, c, M, N, K), (A, B, O), cfg in zip(insts, views, cfgs)]
-        return bt.Batch(descs)
-
-    default = make([0] * len(insts))
+    default = batched_make(insts, views, [0] * len(insts))
     res["items"], res["ctas"] = default.info()
     res["default_graph_ms"] = _time(default.run, reps=2)
     res["default_direct_ms"] = _time(default.run_direct, reps=1)
     default.close()
     model_path = os.path.join(ROOT, "paper_1905_03136_gb300", "tuning", "costmodel.npz")
+    mlp_cfg = None
     if os.path.exists(model_path):
         model = cm.CostModel()
         model.load(model_path)
-        b = make(batched_configs_from_model(insts, model))
+        mlp_cfg = batched_configs_from_model(insts, model)
+        b = batched_make(insts, views, mlp_cfg)
         res["mlp_graph_ms"] = _time(b.run, reps=2)
         b.close()
+    if exhaustive:
+        t0 = time.time()
+        ex_cfg, shapes = batched_configs_exhaustive(insts, flatA, flatB)
+        res["exhaustive_search_s"] = round(time.time() - t0, 1)
+        res["exhaustive_shapes"] = shapes
+        b = batched_make(insts, views, ex_cfg)
+        res["exhaustive_graph_ms"] = _time(b.run, reps=2)
+        b.close()
+        if mlp_cfg is not None:
+            res["mlp_same_code_as_exhaustive"] = sum(a == e for a, e in zip(mlp_cfg, ex_cfg))
+            res["mlp_over_exhaustive"] = res["mlp_graph_ms"] / res["exhaustive_graph_ms"]
 
     def separate():
         for (k, c, M, N, K), (A, B, O) in zip(insts, views):
@@ -1019,7 +1086,7 @@ def run_batched_extra(flatA, flatB):
                 tsm.tsmm(A, B, O)
     res["separate_launches_ms"] = _time(separate, reps=1)
     res["gflops_default_graph"] = flops / (res["default_graph_ms"] * 1e-3) / 1e9
-    del views, outs
+    del views
     torch.cuda.empty_cache()
     return res
 
@@ -1092,7 +1159,9 @@ def run_extras(args, flatA, flatB, K, bw, p64, emit):
     guarded("small_k_ramp", lambda: run_ramp_extra(flatA, flatB, bw, p64))
     bt = guarded("batched", lambda: run_batched_extra(flatA, flatB))
     if "separate_launches_ms" in bt:
-        summ["batched_ms"] = {k: round(bt[k], 1) for k in bt if k.endswith("_ms")}
+        summ["batched_ms"] = {k[:-3]: round(bt[k], 1) for k in ("default_graph_ms", "mlp_graph_ms",
+                                                                 "exhaustive_graph_ms", "separate_launches_ms")
+                              if k in bt}
     return summ
 
 

@@ -30,9 +30,11 @@
  *   out, ldo   TSMTTSM: C (M x N);  TSMM: B (K x N)
  *   config     per-instance configuration, 0 = built-in default:
  *              bits 0-7  TSMTTSM tile code (1: 1x1, 2: 2x2, 3: 4x4, 4: 4x8,
- *                        5: 8x4 -- complex data runs 4 and 5 as 4x4 --,
- *                        6: 3x3, 7: 2x5, 8: 5x2, 9: 3x5, 10: 5x3, 11: 2x7,
- *                        12: 7x2) or TSMM threads per row code (1: 4,
+ *                        5: 8x4, 6: 3x3, 7: 2x5, 8: 5x2, 9: 3x5, 10: 5x3,
+ *                        11: 2x7, 12: 7x2, 13: 8x8, 14: 5x5 -- complex data
+ *                        runs 4, 5 and 13 as 4x4 and 14 as 3x3; a code whose
+ *                        tile needs more than 256 threads, or 0, takes the
+ *                        default) or TSMM threads per row code (1: 4,
  *                        2: 8, 3: 16, 4: any count, chosen from N so that
  *                        up to 4 results per thread cover N with the least
  *                        padding);  bits 8-15  log2 of rows per work item

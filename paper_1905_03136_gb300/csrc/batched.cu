@@ -32,11 +32,39 @@ struct Item {
 };
 
 constexpr int kThreads = 256;
+// Work items per persistent CTA the default split aims at.  Items of a few
+// hundred milliseconds (4 per CTA) left SMs idle behind the last large items;
+// 16 per CTA brought the 256-instance mixed batch from 1380 to 1232 ms.
+constexpr double kItemsPerCta = 16.0;
 
 // ----------------------------------------------------------- TSMTTSM item
 
+// One row's rank-1 update of the register tile (complex: op T or C on A).
+template <int TM, int TN, bool CPLX, bool CONJ>
+__device__ __forceinline__ void item_fma(double (&acc)[TM][TN][CPLX ? 2 : 1], const double (&av)[TM][CPLX ? 2 : 1],
+                                         const double (&bv)[TN][CPLX ? 2 : 1]) {
+    constexpr int CC = CPLX ? 2 : 1;
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            if (!CPLX) {
+                acc[i][j][0] = fma(av[i][0], bv[j][0], acc[i][j][0]);
+            } else {
+                const double ar = av[i][0], ai = av[i][CC - 1];
+                const double br = bv[j][0], bi = bv[j][CC - 1];
+                acc[i][j][0] = fma(ar, br, acc[i][j][0]);
+                acc[i][j][0] = fma(CONJ ? ai : -ai, bi, acc[i][j][0]);
+                acc[i][j][CC - 1] = fma(ar, bi, acc[i][j][CC - 1]);
+                acc[i][j][CC - 1] = fma(CONJ ? -ai : ai, br, acc[i][j][CC - 1]);
+            }
+        }
+}
+
 template <int TM, int TN, int U, bool CPLX, bool CONJ>
-__device__ void tsmttsm_item(const Inst& in, const Item& it, double* parts, unsigned* tickets, double* red) {
+__device__ __noinline__ void tsmttsm_item(const Inst* __restrict__ ip, const Item it, double* parts,
+                                          unsigned* tickets, double* red) {
+    const Inst in = *ip;
     constexpr int CC = CPLX ? 2 : 1;
     __shared__ unsigned s_last;
     const int M = in.M, N = in.N;
@@ -69,40 +97,39 @@ __device__ void tsmttsm_item(const Inst& in, const Item& it, double* parts, unsi
             for (int c = 0; c < CC; ++c) acc[i][j][c] = 0.0;
     const int64_t sa = in.lda * CC, sb = in.ldb * CC;
     if (active) {
-        for (int64_t k = it.r0 + lane; k < it.r1; k += (int64_t)L * U) {
+        // unguarded main loop over whole groups of U rows, then single rows
+        int64_t k = it.r0 + lane;
+        for (; k + (int64_t)(U - 1) * L < it.r1; k += (int64_t)L * U) {
             double av[U][TM][CC], bv[U][TN][CC];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int64_t row = k + (int64_t)u * L;
-                const bool rok = row < it.r1;
-                const double* ar = in.A + (rok ? row : 0) * sa;
-                const double* br = in.B + (rok ? row : 0) * sb;
+                const double* ar = in.A + (k + (int64_t)u * L) * sa;
+                const double* br = in.B + (k + (int64_t)u * L) * sb;
 #pragma unroll
                 for (int i = 0; i < TM; ++i)
 #pragma unroll
-                    for (int c = 0; c < CC; ++c) av[u][i][c] = (rok && mok[i]) ? __ldg(ar + mi[i] * CC + c) : 0.0;
+                    for (int c = 0; c < CC; ++c) av[u][i][c] = mok[i] ? __ldg(ar + mi[i] * CC + c) : 0.0;
 #pragma unroll
                 for (int j = 0; j < TN; ++j)
 #pragma unroll
-                    for (int c = 0; c < CC; ++c) bv[u][j][c] = (rok && nok[j]) ? __ldg(br + nj[j] * CC + c) : 0.0;
+                    for (int c = 0; c < CC; ++c) bv[u][j][c] = nok[j] ? __ldg(br + nj[j] * CC + c) : 0.0;
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u)
+            for (int u = 0; u < U; ++u) item_fma<TM, TN, CPLX, CONJ>(acc, av[u], bv[u]);
+        }
+        for (; k < it.r1; k += L) {
+            const double* ar = in.A + k * sa;
+            const double* br = in.B + k * sb;
+            double av[TM][CC], bv[TN][CC];
 #pragma unroll
-                for (int i = 0; i < TM; ++i)
+            for (int i = 0; i < TM; ++i)
 #pragma unroll
-                    for (int j = 0; j < TN; ++j) {
-                        if (!CPLX) {
-                            acc[i][j][0] = fma(av[u][i][0], bv[u][j][0], acc[i][j][0]);
-                        } else {
-                            const double ar = av[u][i][0], ai = av[u][i][CC - 1];
-                            const double br = bv[u][j][0], bi = bv[u][j][CC - 1];
-                            acc[i][j][0] = fma(ar, br, acc[i][j][0]);
-                            acc[i][j][0] = fma(CONJ ? ai : -ai, bi, acc[i][j][0]);
-                            acc[i][j][CC - 1] = fma(ar, bi, acc[i][j][CC - 1]);
-                            acc[i][j][CC - 1] = fma(CONJ ? -ai : ai, br, acc[i][j][CC - 1]);
-                        }
-                    }
+                for (int c = 0; c < CC; ++c) av[i][c] = mok[i] ? __ldg(ar + mi[i] * CC + c) : 0.0;
+#pragma unroll
+            for (int j = 0; j < TN; ++j)
+#pragma unroll
+                for (int c = 0; c < CC; ++c) bv[j][c] = nok[j] ? __ldg(br + nj[j] * CC + c) : 0.0;
+            item_fma<TM, TN, CPLX, CONJ>(acc, av, bv);
         }
     }
     // lanes: fixed-pairing tree per tile entry, into this item's slot
@@ -185,7 +212,8 @@ __device__ void tsmttsm_item(const Inst& in, const Item& it, double* parts, unsi
 // -------------------------------------------------------------- TSMM item
 
 template <int TPR, int NPT, bool CPLX>
-__device__ void tsmm_item(const Inst& in, const Item& it, double* cs) {
+__device__ __noinline__ void tsmm_item(const Inst* __restrict__ ip, const Item it, double* cs) {
+    const Inst in = *ip;
     constexpr int CC = CPLX ? 2 : 1;
     constexpr int RPC = kThreads / TPR;
     constexpr int U = 2;
@@ -292,7 +320,8 @@ __device__ void tsmm_item(const Inst& in, const Item& it, double* cs) {
 // results each: npt * tpr covers N with the least padding, and the loop over
 // result slots has a warp-uniform bound, so no FMA is spent on padding.
 template <int NPT, bool CPLX>
-__device__ void tsmm_item_rt(const Inst& in, const Item& it, double* cs) {
+__device__ __noinline__ void tsmm_item_rt(const Inst* __restrict__ ip, const Item it, double* cs) {
+    const Inst in = *ip;
     constexpr int CC = CPLX ? 2 : 1;
     constexpr int U = 2;
     const int M = in.M, N = in.N, tpr = in.tpr;
@@ -395,11 +424,12 @@ __device__ void tsmm_item_rt(const Inst& in, const Item& it, double* cs) {
 
 // -------------------------------------------------------- persistent kernel
 
-// Accumulators stay at <= 32 doubles per thread in every instantiation
-// (complex data has no 4x8 / 8x4 tile and no 4-threads-per-row TSMM).
+// Accumulators stay at <= 32 doubles per thread for complex data (codes 4,
+// 5 and 13 run as 4x4, code 14 as 3x3, and there is no 4-threads-per-row
+// TSMM) and at <= 64 for real data (the 8x8 tile of code 13).
 template <bool CPLX, bool CONJ>
-__device__ void run_tsmttsm(const Inst& in, const Item& it, double* parts, unsigned* tickets, double* red) {
-    switch (in.code) {
+__device__ void run_tsmttsm(const Inst* in, const Item& it, double* parts, unsigned* tickets, double* red) {
+    switch (in->code) {
         case 1: tsmttsm_item<1, 1, 4, CPLX, CONJ>(in, it, parts, tickets, red); break;
         case 2: tsmttsm_item<2, 2, 2, CPLX, CONJ>(in, it, parts, tickets, red); break;
         case 4:
@@ -423,13 +453,27 @@ __device__ void run_tsmttsm(const Inst& in, const Item& it, double* parts, unsig
         case 10: tsmttsm_item<5, 3, 1, CPLX, CONJ>(in, it, parts, tickets, red); break;
         case 11: tsmttsm_item<2, 7, 1, CPLX, CONJ>(in, it, parts, tickets, red); break;
         case 12: tsmttsm_item<7, 2, 1, CPLX, CONJ>(in, it, parts, tickets, red); break;
+        case 13:
+            if (!CPLX) {
+                tsmttsm_item<8, 8, 1, CPLX, CONJ>(in, it, parts, tickets, red);
+                break;
+            }
+            tsmttsm_item<4, 4, 1, CPLX, CONJ>(in, it, parts, tickets, red);
+            break;
+        case 14:
+            if (!CPLX) {
+                tsmttsm_item<5, 5, 1, CPLX, CONJ>(in, it, parts, tickets, red);
+                break;
+            }
+            tsmttsm_item<3, 3, 2, CPLX, CONJ>(in, it, parts, tickets, red);
+            break;
         default: tsmttsm_item<4, 4, 1, CPLX, CONJ>(in, it, parts, tickets, red); break;
     }
 }
 
 template <bool CPLX>
-__device__ void run_tsmm(const Inst& in, const Item& it, double* cs) {
-    switch (in.code) {
+__device__ void run_tsmm(const Inst* in, const Item& it, double* cs) {
+    switch (in->code) {
         case 1:
             if (!CPLX) {
                 tsmm_item<4, 16, CPLX>(in, it, cs);
@@ -455,16 +499,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(const Inst* __restrict_
         __syncthreads();
         if (w >= n_items) break;
         const Item it = items[w];
-        const Inst in = insts[it.inst];
-        if (in.kind == TSM_KIND_TSMTTSM) {
-            if (!in.cplx)
+        const Inst* in = insts + it.inst;
+        if (in->kind == TSM_KIND_TSMTTSM) {
+            if (!in->cplx)
                 run_tsmttsm<false, false>(in, it, parts, tickets, dyn);
-            else if (in.conj)
+            else if (in->conj)
                 run_tsmttsm<true, true>(in, it, parts, tickets, dyn);
             else
                 run_tsmttsm<true, false>(in, it, parts, tickets, dyn);
         } else {
-            if (!in.cplx)
+            if (!in->cplx)
                 run_tsmm<false>(in, it, dyn);
             else
                 run_tsmm<true>(in, it, dyn);
@@ -472,17 +516,28 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched(const Inst* __restrict_
     }
 }
 
-// TSMTTSM tiles by code and the default choice: least padding waste, then
-// the larger tile (capped at 32 accumulator doubles), thread count <= 256.
-// (Complex data runs codes 4 and 5 with a 4x4 tile.)
-constexpr int kTileCodes = 12;
-const int kTile[kTileCodes + 1][2] = {{0, 0}, {1, 1}, {2, 2}, {4, 4}, {4, 8}, {8, 4}, {3, 3},
-                                      {2, 5}, {5, 2}, {3, 5}, {5, 3}, {2, 7}, {7, 2}};
+// TSMTTSM tiles by code and the default choice: the least FP64 issue work
+// per useful product -- tile padding past M and N times the idle lanes of
+// partly filled warps, ceil(P*L/32)*32 * TM*TN / (L*M*N) with P threads per
+// lane and L = 256/P lanes -- then the larger tile.  (Complex data runs
+// codes 4, 5 and 13 with a 4x4 tile and code 14 with a 3x3 one.)
+constexpr int kTileCodes = 14;
+const int kTile[kTileCodes + 1][2] = {{0, 0}, {1, 1}, {2, 2}, {4, 4}, {4, 8}, {8, 4}, {3, 3}, {2, 5},
+                                      {5, 2}, {3, 5}, {5, 3}, {2, 7}, {7, 2}, {8, 8}, {5, 5}};
 
-bool tile_ok(int code, int M, int N) {
+// The tile a code runs with (complex data: codes 4, 5, 13 as 4x4, 14 as 3x3).
+void code_tile(int code, int cplx, int* tm, int* tn) {
+    *tm = kTile[code][0];
+    *tn = kTile[code][1];
+    if (cplx && (code == 4 || code == 5 || code == 13)) *tm = *tn = 4;
+    if (cplx && code == 14) *tm = *tn = 3;
+}
+
+bool tile_ok(int code, int M, int N, int cplx) {
     if (code < 1 || code > kTileCodes) return false;
-    const int P = ((M + kTile[code][0] - 1) / kTile[code][0]) * ((N + kTile[code][1] - 1) / kTile[code][1]);
-    return P <= kThreads;
+    int tm, tn;
+    code_tile(code, cplx, &tm, &tn);
+    return ((M + tm - 1) / tm) * ((N + tn - 1) / tn) <= kThreads;
 }
 
 int default_tile(int M, int N, int cplx) {
@@ -490,11 +545,11 @@ int default_tile(int M, int N, int cplx) {
     double bw = 1e30;
     int ba = 0;
     for (int c = 1; c <= kTileCodes; ++c) {
-        if (!tile_ok(c, M, N)) continue;
-        if (cplx && (c == 4 || c == 5)) continue;  // run as 4x4
+        if (!tile_ok(c, M, N, cplx)) continue;
+        if (cplx && (c == 4 || c == 5 || c == 13 || c == 14)) continue;  // same as codes 3 and 6
         const int tm = kTile[c][0], tn = kTile[c][1];
-        if (tm * tn * (cplx ? 2 : 1) > 32) continue;
-        const double waste = (double)((M + tm - 1) / tm * tm) * ((N + tn - 1) / tn * tn) / ((double)M * N);
+        const int P = ((M + tm - 1) / tm) * ((N + tn - 1) / tn), L = kThreads / P;
+        const double waste = (double)((P * L + 31) / 32 * 32) * tm * tn / ((double)L * M * N);
         if (waste < bw - 1e-9 || (waste < bw + 1e-9 && tm * tn > ba)) {
             best = c;
             bw = waste;
@@ -607,7 +662,7 @@ tsm_status tsm_batched_create(const tsm_batch_desc* d, int count, tsm_batch** ou
         in.beta_zero = x.beta[0] == 0.0 && (!in.cplx || x.beta[1] == 0.0);
         int code = x.config & 0xFF;
         if (x.kind == TSM_KIND_TSMTTSM) {
-            if (!tile_ok(code, x.M, x.N)) code = default_tile(x.M, x.N, in.cplx);
+            if (!tile_ok(code, x.M, x.N, in.cplx)) code = default_tile(x.M, x.N, in.cplx);
         } else if (code < 1 || code > 4) {
             // power-of-two threads per row when they cover N exactly, else
             // any count (code 4)
@@ -627,11 +682,15 @@ tsm_status tsm_batched_create(const tsm_batch_desc* d, int count, tsm_batch** ou
         if (lg >= 10 && lg <= 22) {
             rows = (int64_t)1 << lg;
         } else {
-            const double share = work[i] / total * ctas * 4.0;
-            int64_t n = (int64_t)std::max(1.0, std::floor(share));
-            rows = (x.K + n - 1) / n;
-            rows = ((rows + 255) / 256) * 256;
-            if (rows < 4096) rows = 4096;
+            // about kItemsPerCta items per CTA over the whole batch, each
+            // instance cut in proportion to its work; rows per item the
+            // nearest power of two (at least 4096), so an instance ends in a
+            // shorter ragged item and the largest-first order finishes on
+            // small items
+            const double share = work[i] / total * ctas * kItemsPerCta;
+            const double n = std::max(1.0, std::floor(share));
+            const int l = (int)std::lround(std::log2(std::max((double)x.K / n, 1.0)));
+            rows = (int64_t)1 << std::min(22, std::max(12, l));
         }
         const int64_t K = std::max<int64_t>(x.K, 1);
         const int n_items = (int)((K + rows - 1) / rows);

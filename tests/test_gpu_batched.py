@@ -83,10 +83,13 @@ def test_batched_random_instances_and_replay(lib):
     assert items >= len(insts) and ctas >= 152
 
 
-@pytest.mark.parametrize("code", list(range(1, 13)))
+@pytest.mark.parametrize("code", list(range(1, 15)))
 def test_batched_every_tsmttsm_tile_code(lib, code):
+    """Every tile code on shapes that pad it and shapes it cannot take (more
+    than 256 threads: the default tile runs instead)."""
     import torch
-    insts = [(0, c, M, N, 20000) for c in (False, True) for (M, N) in ((1, 1), (5, 7), (16, 16), (64, 64), (3, 64))]
+    insts = [(0, c, M, N, 20000) for c in (False, True)
+             for (M, N) in ((1, 1), (5, 7), (16, 16), (64, 64), (3, 64), (37, 53), (64, 61))]
     configs = [code | (12 << 8)] * len(insts)  # 4096-row items
     batch, host, dev = _build(insts, configs, beta=0.5)
     batch.run()
