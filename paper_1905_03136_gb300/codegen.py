@@ -248,6 +248,7 @@ def emit_tsmttsm(s):
     w = o.append
     w("template <bool CONJ>")
     w("__global__ void __launch_bounds__(%d) %s(const TsmttsmArgs a) {" % (BLK, name))
+    w("    tsmttsm_begin(a);")
     w("    constexpr int PM = %d, PN = %d, P = %d, L = %d;" % (PM, PN, P, L))
     w("    const int t = threadIdx.x;")
     w("    const int lane = t / P, p = t - lane * P;")
@@ -330,11 +331,10 @@ def emit_tsmttsm(s):
     w("")
     w("cudaError_t launch_%s(const TsmttsmArgs& a, int grid, cudaStream_t s) {" % name)
     if cplx:
-        w("    if (a.conj) %s<true><<<grid, %d, 0, s>>>(a);" % (name, BLK))
-        w("    else %s<false><<<grid, %d, 0, s>>>(a);" % (name, BLK))
+        w("    if (a.conj) return launch_pdl(%s<true>, grid, %d, 0, s, a);" % (name, BLK))
+        w("    return launch_pdl(%s<false>, grid, %d, 0, s, a);" % (name, BLK))
     else:
-        w("    %s<false><<<grid, %d, 0, s>>>(a);" % (name, BLK))
-    w("    return cudaGetLastError();")
+        w("    return launch_pdl(%s<false>, grid, %d, 0, s, a);" % (name, BLK))
     w("}")
     w("int occ_%s(int, int) {" % name)
     w("    int n = 0;")
@@ -367,6 +367,7 @@ def emit_tsmm(s):
         w("template <bool GEN>")
     w("__global__ void __launch_bounds__(%d) %s(const TsmmArgs a) {" % (BLK, name))
     w("    extern __shared__ double cs[];")
+    w("    tsmm_begin(a);")
     w("    tsmm_stage_c<%d>(a, cs);" % CC)
     w("    constexpr int TPR = %d, RPC = %d;" % (TPR, RPC))
     w("    const int r = threadIdx.x / TPR, q = threadIdx.x - r * TPR;")
@@ -442,17 +443,14 @@ def emit_tsmm(s):
             w("    cudaError_t e = cudaFuncSetAttribute(gen ? %s<true> : %s<false>, "
               "cudaFuncAttributeMaxDynamicSharedMemorySize, %d);" % (name, name, smem))
             w("    if (e != cudaSuccess) return e;")
-        w("    if (gen)")
-        w("        %s<true><<<grid, %d, %d, s>>>(a);" % (name, BLK, smem))
-        w("    else")
-        w("        %s<false><<<grid, %d, %d, s>>>(a);" % (name, BLK, smem))
+        w("    if (gen) return launch_pdl(%s<true>, grid, %d, %d, s, a);" % (name, BLK, smem))
+        w("    return launch_pdl(%s<false>, grid, %d, %d, s, a);" % (name, BLK, smem))
     else:
         if smem > 48 * 1024:
             w("    cudaError_t e = cudaFuncSetAttribute(%s, cudaFuncAttributeMaxDynamicSharedMemorySize, %d);"
               % (name, smem))
             w("    if (e != cudaSuccess) return e;")
-        w("    %s<<<grid, %d, %d, s>>>(a);" % (name, BLK, smem))
-    w("    return cudaGetLastError();")
+        w("    return launch_pdl(%s, grid, %d, %d, s, a);" % (name, BLK, smem))
     w("}")
     w("int occ_%s(int, int) {" % name)
     if smem > 48 * 1024:

@@ -88,6 +88,87 @@ tsm_status workspace_get(cudaStream_t stream, size_t partial_bytes, int tickets,
     return TSM_OK;
 }
 
+// ------------------------------------------------- early-start bookkeeping
+
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* e = getenv("TSM_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
+Range operand_range(const void* p, int64_t rows, int64_t ld, int cols, int cplx) {
+    Range r = {0, 0};
+    if (!p || rows <= 0 || cols <= 0) return r;
+    r.lo = (uintptr_t)p;
+    r.hi = r.lo + (uintptr_t)(((uint64_t)(rows - 1) * (uint64_t)ld + (uint64_t)cols) * (cplx ? 16u : 8u));
+    return r;
+}
+
+namespace {
+
+bool overlaps(const Range& a, const Range& b) { return a.lo < b.hi && b.lo < a.hi; }
+
+// A fixed table (no allocation, so the no-allocation entry point can use
+// it); the least recently used record makes room for a new stream.
+constexpr int kPdlOuts = 8;
+struct PdlRecord {
+    int dev;
+    cudaStream_t stream;
+    unsigned long long used;
+    Range out[kPdlOuts];  // outputs since the last barrier, the barrier's first
+    int n;
+};
+constexpr int kPdlRecords = 64;
+PdlRecord g_pdl[kPdlRecords];
+unsigned long long g_pdl_clock = 0;
+std::mutex g_pdl_mutex;
+
+PdlRecord* pdl_find(int dev, cudaStream_t s) {
+    for (int i = 0; i < kPdlRecords; ++i)
+        if (g_pdl[i].used && g_pdl[i].dev == dev && g_pdl[i].stream == s) return &g_pdl[i];
+    return nullptr;
+}
+
+}  // namespace
+
+std::mutex& pdl_mutex() { return g_pdl_mutex; }
+
+int pdl_early(cudaStream_t s, const Range* in, int nin) {
+    if (!pdl_enabled()) return 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    const PdlRecord* r = pdl_find(dev, s);
+    if (!r || r->n >= kPdlOuts) return 0;
+    for (int j = 0; j < r->n; ++j)
+        for (int i = 0; i < nin; ++i)
+            if (overlaps(in[i], r->out[j])) return 0;
+    return 1;
+}
+
+void pdl_note(cudaStream_t s, Range out, int early) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    PdlRecord* r = pdl_find(dev, s);
+    if (!r) {
+        r = &g_pdl[0];
+        for (int i = 0; i < kPdlRecords; ++i) {
+            if (!g_pdl[i].used) {
+                r = &g_pdl[i];
+                break;
+            }
+            if (g_pdl[i].used < r->used) r = &g_pdl[i];
+        }
+        r->dev = dev;
+        r->stream = s;
+        early = 0;  // a new record starts at this product
+    }
+    r->used = ++g_pdl_clock;
+    if (!early || r->n >= kPdlOuts) r->n = 0;
+    r->out[r->n++] = out;
+}
+
 static tsm_status release_all() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return TSM_ERR_NO_DEVICE;
@@ -315,8 +396,12 @@ tsm_status run_tsmttsm(tsm_op opA, tsm_dtype dtype, int M, int N, int64_t K, con
     a.ws = ws->partials;
     a.ticket = ws->tickets;
     a.final_pass = tsm_tsmttsm_kernels_per_call(dtype, M, N, g) == 2 ? 1 : 0;
+    const Range in[2] = {operand_range(A, K, lda, M, cplx), operand_range(B, K, ldb, N, cplx)};
+    std::lock_guard<std::mutex> lock(pdl_mutex());
+    a.early = pdl_early(stream, in, 2);
     if (var.tsmttsm(a, g, stream) != cudaSuccess) return TSM_ERR_LAUNCH;
     if (a.final_pass && launch_tsmttsm_final(a, g, cplx, stream) != cudaSuccess) return TSM_ERR_LAUNCH;
+    pdl_note(stream, operand_range(C, M, ldc, N, cplx), a.early);
     return TSM_OK;
 }
 
@@ -368,7 +453,9 @@ tsm_status run_tsmm(tsm_op opC, tsm_dtype dtype, int M, int N, int64_t K, const 
     a.beta_i = cplx ? beta[1] : 0.0;
     a.beta_zero = beta_zero;
     a.beta_one = beta[0] == 1.0 && (!cplx || beta[1] == 0.0);
+    std::lock_guard<std::mutex> lock(pdl_mutex());
     if (var.tsmm(a, g, stream) != cudaSuccess) return TSM_ERR_LAUNCH;
+    pdl_note(stream, operand_range(B, K, ldb, N, cplx), 0);
     return TSM_OK;
 }
 

@@ -23,6 +23,7 @@ namespace {
 template <int TM, int TN, int U, bool CPLX, bool CONJ>
 __global__ void __launch_bounds__(kBlock) k_tsmttsm(const TsmttsmArgs a) {
     constexpr int CC = CPLX ? 2 : 1;
+    tsmttsm_begin(a);
     const int M = a.M, N = a.N;
     const int PM = (M + TM - 1) / TM, PN = (N + TN - 1) / TN, P = PM * PN;
     const int L = kBlock / P;
@@ -131,11 +132,8 @@ __global__ void __launch_bounds__(kBlock) k_tsmttsm(const TsmttsmArgs a) {
 
 template <int TM, int TN, int U, bool CPLX>
 cudaError_t launch_tsmttsm(const TsmttsmArgs& a, int grid, cudaStream_t s) {
-    if (CPLX && a.conj)
-        k_tsmttsm<TM, TN, U, CPLX, true><<<grid, kBlock, 0, s>>>(a);
-    else
-        k_tsmttsm<TM, TN, U, CPLX, false><<<grid, kBlock, 0, s>>>(a);
-    return cudaGetLastError();
+    if (CPLX && a.conj) return launch_pdl(k_tsmttsm<TM, TN, U, CPLX, true>, grid, kBlock, 0, s, a);
+    return launch_pdl(k_tsmttsm<TM, TN, U, CPLX, false>, grid, kBlock, 0, s, a);
 }
 
 template <int TM, int TN, int U, bool CPLX>

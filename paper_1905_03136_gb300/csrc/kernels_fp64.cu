@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(kBlock) k_tsmm(const TsmmArgs a) {
     constexpr int RPC = kBlock / TPR;  // rows per CTA per unrolled step
     extern __shared__ double cs[];     // alpha * C, M x N (x CC)
     const int N = a.N, M = a.M;
+    tsmm_begin(a);
     tsmm_stage_c<CC>(a, cs);
 
     const int r = threadIdx.x / TPR, q = threadIdx.x - r * TPR;
@@ -137,8 +138,7 @@ cudaError_t launch_tsmm_as(const TsmmArgs& a, int grid, cudaStream_t s) {
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_tsmm<TPR, NPT, U, CPLX, GEN><<<grid, kBlock, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(k_tsmm<TPR, NPT, U, CPLX, GEN>, grid, kBlock, smem, s, a);
 }
 
 template <int TPR, int NPT, int U, bool CPLX>
@@ -263,6 +263,8 @@ namespace {
 // however many CTAs wrote partials.
 template <int CC>
 __global__ void __launch_bounds__(256) k_tsmttsm_final(const TsmttsmArgs a, int G, int S) {
+    pdl_trigger();
+    pdl_wait();  // the partials of the launch before
     const int MN = a.M * a.N;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int o = gt / S, s = gt - o * S;  // S divides 32: an entry's lanes share a warp
@@ -287,11 +289,8 @@ cudaError_t launch_tsmttsm_final(const TsmttsmArgs& a, int grid, int cplx, cudaS
     while (S < 32 && grid >= 16 * S) S *= 2;  // at least 8 partials per lane
     const int threads = MN * S;
     const int blocks = (threads + 255) / 256;
-    if (cplx)
-        k_tsmttsm_final<2><<<blocks, 256, 0, s>>>(a, grid, S);
-    else
-        k_tsmttsm_final<1><<<blocks, 256, 0, s>>>(a, grid, S);
-    return cudaGetLastError();
+    if (cplx) return launch_pdl(k_tsmttsm_final<2>, blocks, 256, 0, s, a, grid, S);
+    return launch_pdl(k_tsmttsm_final<1>, blocks, 256, 0, s, a, grid, S);
 }
 
 cudaError_t launch_scale_small(double* C, int rows, int cols, int64_t ld, int cplx, double br, double bi,

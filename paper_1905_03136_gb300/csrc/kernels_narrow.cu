@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(kBlock) k_tsmttsm_narrow(const TsmttsmArgs a, 
     typedef Group<M, N, CC, VW> Gp;
     constexpr int R = Gp::R, EA = Gp::EA, EB = Gp::EB, MNC = M * N * CC;
     constexpr int VP = next_pow2(MNC);  // values per lane, padded for the warp reduction
+    tsmttsm_begin(a);
     double acc[VP];
 #pragma unroll
     for (int e = 0; e < VP; ++e) acc[e] = 0.0;
@@ -312,6 +313,7 @@ __global__ void __launch_bounds__(kBlock) k_tsmttsm_narrow(const TsmttsmArgs a, 
     const int e = lane >> (5 - L);
     if ((lane & ((32 >> L) - 1)) == 0 && e < MNC) red[warp * MNC + e] = acc[0];
     __syncthreads();
+    pdl_wait();  // the previous launch on the stream may still use the workspace
     if (t < MNC) {
         double s = red[t];
 #pragma unroll
@@ -331,10 +333,8 @@ cudaError_t launch_tsmttsm_narrow(const TsmttsmArgs& a, int grid, cudaStream_t s
     if (a.M != M || a.N != N) return cudaErrorInvalidValue;
     const int vec = narrow_vec_ok<M, N, CC, VW>(a.A, a.lda, a.B, a.ldb) ? 1 : 0;
     if (CC == 2 && a.conj)
-        k_tsmttsm_narrow<M, N, CC, true, VW, U, PF, WIN><<<grid, kBlock, 0, s>>>(a, vec);
-    else
-        k_tsmttsm_narrow<M, N, CC, false, VW, U, PF, WIN><<<grid, kBlock, 0, s>>>(a, vec);
-    return cudaGetLastError();
+        return launch_pdl(k_tsmttsm_narrow<M, N, CC, true, VW, U, PF, WIN>, grid, kBlock, 0, s, a, vec);
+    return launch_pdl(k_tsmttsm_narrow<M, N, CC, false, VW, U, PF, WIN>, grid, kBlock, 0, s, a, vec);
 }
 
 template <int M, int N, int CC, int VW, int U, bool PF, bool WIN>
@@ -352,6 +352,7 @@ template <int M, int N, int CC, int VW, int U, bool PF>
 __global__ void __launch_bounds__(kBlock) k_tsmm_narrow(const TsmmArgs a, int vec) {
     typedef Group<M, N, CC, VW> Gp;
     constexpr int R = Gp::R, EA = Gp::EA, EB = Gp::EB;
+    tsmm_begin(a);
     // alpha * C in registers
     double cr[M * N * CC];
 #pragma unroll
@@ -531,8 +532,7 @@ template <int M, int N, int CC, int VW, int U, bool PF>
 cudaError_t launch_tsmm_narrow(const TsmmArgs& a, int grid, cudaStream_t s) {
     if (a.M != M || a.N != N) return cudaErrorInvalidValue;
     const int vec = narrow_vec_ok<M, N, CC, VW>(a.A, a.lda, a.B, a.ldb) ? 1 : 0;
-    k_tsmm_narrow<M, N, CC, VW, U, PF><<<grid, kBlock, 0, s>>>(a, vec);
-    return cudaGetLastError();
+    return launch_pdl(k_tsmm_narrow<M, N, CC, VW, U, PF>, grid, kBlock, 0, s, a, vec);
 }
 
 template <int M, int N, int CC, int VW, int U, bool PF>

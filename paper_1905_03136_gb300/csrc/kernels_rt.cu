@@ -52,6 +52,7 @@ __global__ void __launch_bounds__(kBlock) k_tsmm_rt(const TsmmArgs a, const int 
     constexpr int CC = CPLX ? 2 : 1;
     extern __shared__ double cs[];  // alpha * C, M x N (x CC)
     const int N = a.N, M = a.M;
+    tsmm_begin(a);
     tsmm_stage_c<CC>(a, cs);
 
     const int rpc = kBlock / tpr;  // rows per CTA per unrolled step
@@ -148,8 +149,7 @@ cudaError_t launch_tsmm_rt_as(const TsmmArgs& a, int grid, cudaStream_t s) {
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_tsmm_rt<NPT, U, CPLX, GEN><<<grid, kBlock, smem, s>>>(a, tpr);
-    return cudaGetLastError();
+    return launch_pdl(k_tsmm_rt<NPT, U, CPLX, GEN>, grid, kBlock, smem, s, a, tpr);
 }
 
 template <int NPT, int U, bool CPLX>

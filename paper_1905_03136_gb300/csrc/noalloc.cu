@@ -109,7 +109,12 @@ extern "C" tsm_status tsm_tsmttsm_noalloc(tsm_op opA, tsm_dtype dtype, int M, in
     a.ticket = ticket;
     // many partials: a separate final kernel sums them (it allocates nothing)
     a.final_pass = tsm_tsmttsm_kernels_per_call(dtype, M, N, grid) == 2 ? 1 : 0;
+    // the ticket reset above already orders this launch after the previous
+    // one; the record lets the next product know what this one writes
+    std::lock_guard<std::mutex> lock(pdl_mutex());
+    a.early = 0;
     if (var->tsmttsm(a, grid, s) != cudaSuccess) return TSM_ERR_LAUNCH;
     if (a.final_pass && launch_tsmttsm_final(a, grid, cplx, s) != cudaSuccess) return TSM_ERR_LAUNCH;
+    pdl_note(s, operand_range(C, M, ldc, N, cplx), 0);
     return TSM_OK;
 }

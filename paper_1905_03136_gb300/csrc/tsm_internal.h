@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <vector>
 
 #include "tsm.h"
@@ -29,6 +30,8 @@ struct TsmttsmArgs {
     unsigned* ticket; // one counter, zero between launches
     int final_pass;   // 1: CTAs only write their partials; a separate final
                       // kernel (launch_tsmttsm_final) sums them afterwards
+    int early;        // 1: A and B may be read before the previous launch on
+                      // the stream completes (pdl_wait in fp64_common.cuh)
 };
 
 // Arguments of one TSMM launch.
@@ -45,6 +48,29 @@ struct TsmmArgs {
     int beta_zero;
     int beta_one;     // beta == 1 exactly: the old B value starts the FMA chain as it is
 };
+
+// Programmatic dependent launch.  The product kernels are launched with
+// programmatic stream serialization, so the next product on the stream may
+// be scheduled while this one drains; the kernels' pdl_trigger / pdl_wait
+// (fp64_common.cuh) keep every dependency.  TSM_PDL=0 in the environment
+// launches them the ordinary way.
+bool pdl_enabled();
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 typedef cudaError_t (*TsmttsmLaunch)(const TsmttsmArgs&, int grid, cudaStream_t);
 typedef cudaError_t (*TsmmLaunch)(const TsmmArgs&, int grid, cudaStream_t);
@@ -84,6 +110,23 @@ struct DeviceInfo {
     size_t smem_optin;
 };
 const DeviceInfo& device_info();
+
+// Byte range [lo, hi) of a strided operand.
+struct Range {
+    uintptr_t lo, hi;
+};
+Range operand_range(const void* p, int64_t rows, int64_t ld, int cols, int cplx);
+
+// Early-start bookkeeping for launch_pdl: per (device, stream), the outputs
+// of the products launched since the last barrier (a product that waited at
+// its start), which may still be running when the next one starts.  Call
+// both with pdl_mutex() held, around the launch.  pdl_early is 1 when none
+// of those outputs overlaps `in`; 0 when one does, when the list is full,
+// or when the stream has no record (nothing known).  pdl_note records a
+// launched product (early: whether it read before waiting).
+std::mutex& pdl_mutex();
+int pdl_early(cudaStream_t s, const Range* in, int nin);
+void pdl_note(cudaStream_t s, Range out, int early);
 
 // Per-(device, stream) scratch: partial sums + reduction tickets.
 struct Workspace {
