@@ -194,7 +194,7 @@ def _kernel_source_hash(variant_name):
     elif "_rt_" in variant_name:
         files.append("csrc/kernels_rt.cu")
     else:
-        files.append("csrc/kernels_fp64.cu")
+        files += ["csrc/kernels_fp64.cu", "csrc/fp64_tsmttsm.cuh"]
     for name in files:
         with open(os.path.join(pkg, name), "rb") as f:
             h.update(f.read())

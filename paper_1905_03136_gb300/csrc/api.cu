@@ -98,6 +98,42 @@ bool pdl_enabled() {
     return on;
 }
 
+namespace {
+struct OccKey {
+    const void* kernel;
+    int block;
+    size_t smem;
+    bool operator<(const OccKey& o) const {
+        if (kernel != o.kernel) return kernel < o.kernel;
+        if (block != o.block) return block < o.block;
+        return smem < o.smem;
+    }
+};
+std::mutex g_occ_mutex;
+std::map<std::pair<int, OccKey>, int> g_occ;  // (device, kernel shape) -> resident CTAs per SM
+}  // namespace
+
+bool pdl_allowed(const void* kernel, int grid, int block, size_t smem) {
+    if (!pdl_enabled()) return false;
+    const DeviceInfo& di = device_info();
+    const auto key = std::make_pair(di.device, OccKey{kernel, block, smem});
+    int occ = 0;
+    {
+        std::lock_guard<std::mutex> lock(g_occ_mutex);
+        auto it = g_occ.find(key);
+        if (it != g_occ.end()) {
+            occ = it->second;
+        } else {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, smem) != cudaSuccess) {
+                cudaGetLastError();
+                occ = 0;
+            }
+            g_occ[key] = occ;
+        }
+    }
+    return occ > 0 && (int64_t)grid >= (int64_t)occ * di.sm_count;
+}
+
 Range operand_range(const void* p, int64_t rows, int64_t ld, int cols, int cplx) {
     Range r = {0, 0};
     if (!p || rows <= 0 || cols <= 0) return r;

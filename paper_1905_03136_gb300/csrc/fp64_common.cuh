@@ -68,26 +68,23 @@ __device__ __forceinline__ void warp_reduce_scatter(double* v, int lane) {
 // product kernel waits for the previous launch on its stream to complete,
 // with its writes visible (pdl_wait), before it writes global memory -- its
 // partials, C, or B -- so its own completion implies that of every earlier
-// launch.  It lets the next launch be scheduled (pdl_trigger: that launch's
-// CTAs take SMs as this kernel's CTAs leave) at its start, or, when it
-// waits at its start, right after that wait: such a launch is a barrier, and
-// the launches after it can only overlap it and one another.  A TSMTTSM
-// reads its inputs before the wait only when the host found that no product
-// launched since the last barrier wrote them.  Without the launch attribute
-// both instructions are no-ops.
+// launch.  A TSMTTSM lets the next launch be scheduled (pdl_trigger) once
+// its main loop is done: the next product's CTAs then start streaming while
+// this one reduces across CTAs, but two products never stream at the same
+// time.  A TSMM triggers only by exiting.  A launch that waits at its start
+// is a barrier: the launches after it can only overlap it and one another.
+// A TSMTTSM reads its inputs before waiting only when the host found that
+// no product launched since the last barrier wrote them.  Without the
+// launch attribute both instructions are no-ops.
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 __device__ __forceinline__ void tsmttsm_begin(const TsmttsmArgs& a) {
     if (!a.early) pdl_wait();
-    pdl_trigger();
 }
 
 // TSMM's main loop writes B, so it always waits first (a barrier).
-__device__ __forceinline__ void tsmm_begin(const TsmmArgs&) {
-    pdl_wait();
-    pdl_trigger();
-}
+__device__ __forceinline__ void tsmm_begin(const TsmmArgs&) { pdl_wait(); }
 
 constexpr int log2_pow2(int v) { return v <= 1 ? 0 : 1 + log2_pow2(v >> 1); }
 constexpr int next_pow2(int v) { return v <= 1 ? 1 : 2 * next_pow2((v + 1) >> 1); }
@@ -201,7 +198,8 @@ __device__ __forceinline__ void tsmttsm_finish(const TsmttsmArgs& a, const doubl
     const int t = threadIdx.x;
     const int MNc = M * N * CC;
     double* part = a.ws + (int64_t)blockIdx.x * MNc;
-    pdl_wait();  // the previous launch on the stream may still use the workspace
+    pdl_trigger();  // the main loop is done
+    pdl_wait();     // the previous launch on the stream may still use the workspace
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll

@@ -303,6 +303,8 @@ __global__ void __launch_bounds__(kBlock) k_tsmttsm_narrow(const TsmttsmArgs a, 
         }
     }
 
+    pdl_trigger();  // the main loop is done: the next launch may be scheduled
+
     // In-CTA reduction: recursive halving across the 32 lanes (about VP
     // adds per lane instead of 5 per value), then the 8 warp sums in warp
     // order.  Every pairing is fixed, so the CTA partial repeats bit for bit.

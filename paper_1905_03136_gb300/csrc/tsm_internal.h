@@ -55,6 +55,11 @@ struct TsmmArgs {
 // (fp64_common.cuh) keep every dependency.  TSM_PDL=0 in the environment
 // launches them the ordinary way.
 bool pdl_enabled();
+// Whether a launch of `grid` CTAs may start early.  A grid smaller than the
+// kernel's resident capacity (occupancy x SMs) may not: its CTAs would be
+// placed as the previous kernel's CTAs leave, the SMs that free up first
+// taking several, and a grid sized for k CTAs per SM would run unevenly.
+bool pdl_allowed(const void* kernel, int grid, int block, size_t smem);
 
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
@@ -68,7 +73,7 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t sme
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    cfg.numAttrs = pdl_allowed((const void*)kernel, grid, block, smem) ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
