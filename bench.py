@@ -858,9 +858,9 @@ def run_gs_extra(flatA, flatB, K, bw, p64):
     # what a single fused kernel could remove at most: one launch and the C
     # round trip through L2)
     small = []
-    for (cplx, M, N) in ((True, 32, 32), (False, 8, 8)):
+    for (cplx, M, N) in ((True, 32, 32), (False, 8, 8), (True, 64, 64)):
         c = 2 if cplx else 1
-        for Ks in (10 ** 4, 10 ** 5, 10 ** 6):
+        for Ks in (3000, 10 ** 4, 1 << 15, 10 ** 5, 10 ** 6):
             A = flatA[: Ks * M * c]
             B = Bw[: Ks * N * c]
             B.copy_(flatB[: Ks * N * c])
@@ -869,13 +869,19 @@ def run_gs_extra(flatA, flatB, K, bw, p64):
             A, B = A.view(Ks, M), B.view(Ks, N)
             C = torch.empty((M, N), dtype=A.dtype, device=A.device)
             t_gs = _time(lambda: tsm.gs_step(A, B, C), reps=50, warm=5)
+            t_two = _time(lambda: tsm.gs_step(A, B, C, mode="two_products"), reps=50, warm=5)
+            t_fused = _time(lambda: tsm.gs_step(A, B, C, mode="fused"), reps=50, warm=5)
             t_1 = _time(lambda: tsm.tsmttsm(A, B, C, op="C"), reps=50, warm=5)
             t_2 = _time(lambda: tsm.tsmm(A, C, B, -1.0, 1.0), reps=50, warm=5)
             small.append({"dtype": "c64" if cplx else "r64", "M": M, "N": N, "K": Ks, "gs_us": round(t_gs * 1e3, 2),
+                          "two_products_us": round(t_two * 1e3, 2), "fused_us": round(t_fused * 1e3, 2),
                           "tsmttsm_us": round(t_1 * 1e3, 2), "tsmm_us": round(t_2 * 1e3, 2)})
+    tsm.gs_status()
     del Bw
     torch.cuda.empty_cache()
-    return {"what": "tsm_gs_step: TSMTTSM (op C) then TSMM (alpha=-1, beta=1) on one stream, C on the device",
+    return {"what": "tsm_gs_step: TSMTTSM (op C) then TSMM (alpha=-1, beta=1) on one stream, C on the device; "
+                    "small_k: the default path (fused for K <= 2^15), the two products, the fused kernel, and "
+                    "each product alone",
             "roofline_pct_all": 100 * ideal / meas, "calls": out, "small_k": small}
 
 

@@ -197,7 +197,8 @@ tsm_status tsm_tsmm_ex(tsm_op opC, tsm_dtype dtype, int M, int N, int64_t K,
  * reads it from device memory once per CTA into shared memory.  Both
  * products use the variants the tuning table selects; the two launches are
  * enqueued on `stream` back to back (no host synchronisation, capturable in
- * a CUDA graph).  With A not orthonormal the same two products run (one
+ * a CUDA graph).  For K <= 2^15 the step runs as one fused cooperative
+ * kernel instead (tsm_gs_step_ex).  With A not orthonormal the same two products run (one
  * classical Gram-Schmidt projection).
  * Errors: as tsm_tsmttsm / tsm_tsmm; C == NULL -> INVALID_VALUE; every check
  * runs before the first launch, so on an error B and C are untouched.  C must
@@ -206,6 +207,45 @@ tsm_status tsm_tsmm_ex(tsm_op opC, tsm_dtype dtype, int M, int N, int64_t K,
 tsm_status tsm_gs_step(tsm_dtype dtype, int M, int N, int64_t K, const void *A,
                        int64_t lda, void *B, int64_t ldb, void *C, int64_t ldc,
                        tsm_stream_t stream);
+
+/* How tsm_gs_step_ex runs the step. */
+typedef enum {
+    TSM_GS_AUTO = 0,         /* fused for K <= 2^15, else two products */
+    TSM_GS_TWO_PRODUCTS = 1, /* the TSMTTSM and TSMM launches described above */
+    TSM_GS_FUSED = 2         /* one cooperative kernel (below) */
+} tsm_gs_mode;
+
+/*
+ * tsm_gs_step with a choice of path; tsm_gs_step is TSM_GS_AUTO.  The fused
+ * path is one cooperative launch in which every CTA owns a contiguous range
+ * of rows: it forms its partial of C over its rows, all CTAs meet at a grid
+ * barrier, CTA b sums a slice of C's entries over the partials in a fixed
+ * order and stores them in C, all meet again, and each CTA then updates its
+ * own rows of B with -C staged in shared memory.  At small K the second pass
+ * finds its rows in L2, and the step is one launch instead of two.  The
+ * barrier waits are bounded (tsm_gs_set_timeout); a wait that gives up
+ * leaves B and C unspecified and an error word that tsm_gs_status reports.
+ * Results of both paths are deterministic (fixed reduction orders) but not
+ * bitwise equal to each other.  Arguments, layout, ownership and errors as
+ * tsm_gs_step; an unknown mode -> INVALID_VALUE.
+ */
+tsm_status tsm_gs_step_ex(tsm_dtype dtype, int M, int N, int64_t K, const void *A,
+                          int64_t lda, void *B, int64_t ldb, void *C, int64_t ldc,
+                          tsm_gs_mode mode, tsm_stream_t stream);
+
+/*
+ * Synchronizes `stream` and reports whether a fused Gram-Schmidt step on it
+ * hit a barrier wait that gave up (TSM_ERR_TIMEOUT), TSM_OK otherwise.
+ * Clears the word.
+ */
+tsm_status tsm_gs_status(tsm_stream_t stream);
+
+/*
+ * Test hook: every barrier wait of later fused steps (all streams) limited
+ * to `timeout_cycles` SM clock cycles; <= 0 restores the default of about
+ * two seconds.
+ */
+tsm_status tsm_gs_set_timeout(int64_t timeout_cycles);
 
 /* The variant index and grid the library would use for this shape
  * (tuning table first, then the built-in heuristic). */

@@ -87,9 +87,13 @@ def tsmm(A, Cm, B=None, alpha=1.0, beta=0.0, stream=None, variant=-1, grid=0):
     return B
 
 
-def gs_step(A, B, C=None, stream=None):
+GS_MODES = {"auto": 0, "two_products": 1, "fused": 2}
+
+
+def gs_step(A, B, C=None, stream=None, mode="auto"):
     """One block Gram-Schmidt projection in place: C = A^H B, B -= A C.
-    Returns C (M x N, on the device)."""
+    Returns C (M x N, on the device).  mode: "auto", "two_products" or
+    "fused" (tsm_gs_step_ex)."""
     torch = _torch()
     dt = _dtype_code(A)
     K, M = A.shape
@@ -100,9 +104,20 @@ def gs_step(A, B, C=None, stream=None):
         C = torch.empty((M, N), dtype=A.dtype, device=A.device)
     elif C.shape != (M, N) or _dtype_code(C) != dt:
         raise ValueError("C must be M x N with A's dtype")
-    call("tsm_gs_step", dt, M, N, K, ctypes.c_void_p(A.data_ptr()), _ld(A, "A"), ctypes.c_void_p(B.data_ptr()),
-         _ld(B, "B"), ctypes.c_void_p(C.data_ptr()), _ld(C, "C"), _stream(stream))
+    call("tsm_gs_step_ex", dt, M, N, K, ctypes.c_void_p(A.data_ptr()), _ld(A, "A"), ctypes.c_void_p(B.data_ptr()),
+         _ld(B, "B"), ctypes.c_void_p(C.data_ptr()), _ld(C, "C"), GS_MODES[mode], _stream(stream))
     return C
+
+
+def gs_status(stream=None):
+    """Synchronizes the stream; raises TSM_ERR_TIMEOUT if a fused step on it
+    gave up a barrier wait (tsm_gs_status)."""
+    call("tsm_gs_status", _stream(stream))
+
+
+def gs_set_timeout(cycles):
+    """Test hook: barrier wait budget of later fused steps (<= 0: default)."""
+    call("tsm_gs_set_timeout", int(cycles))
 
 
 DIST = {"uniform": 0, "loguniform": 1, "smallint": 2, "ones": 3}

@@ -52,6 +52,9 @@ SIGNATURES = {
     "tsm_tsmttsm_ex": (i32, [i32, i32, i32, i32, i64, dp, vp, i64, vp, i64, dp, vp, i64, i32, i32, vp]),
     "tsm_tsmm_ex": (i32, [i32, i32, i32, i32, i64, dp, vp, i64, vp, i64, dp, vp, i64, i32, i32, vp]),
     "tsm_gs_step": (i32, [i32, i32, i32, i64, vp, i64, vp, i64, vp, i64, vp]),
+    "tsm_gs_step_ex": (i32, [i32, i32, i32, i64, vp, i64, vp, i64, vp, i64, i32, vp]),
+    "tsm_gs_status": (i32, [vp]),
+    "tsm_gs_set_timeout": (i32, [i64]),
     "tsm_variant_shape": (i32, [i32, i32, i32, i32, i32, ctypes.POINTER(VariantInfo)]),
     "tsm_status_string": (ctypes.c_char_p, [i32]),
     "tsm_version": (ctypes.c_char_p, []),

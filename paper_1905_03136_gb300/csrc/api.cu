@@ -81,6 +81,7 @@ tsm_status workspace_get(cudaStream_t stream, size_t partial_bytes, int tickets,
             return TSM_ERR_ALLOC;
         }
         if (cudaMemset(w->tickets, 0, sizeof(unsigned) * tc) != cudaSuccess) return TSM_ERR_LAUNCH;
+        w->gs_gen = 0u;  // the barrier flag starts at zero again
         w->partial_bytes = pb;
         w->ticket_count = tc;
     }
@@ -528,19 +529,30 @@ tsm_status tsm_tsmm_ex(tsm_op opC, tsm_dtype dtype, int M, int N, int64_t K, con
                     (cudaStream_t)stream);
 }
 
-tsm_status tsm_gs_step(tsm_dtype dtype, int M, int N, int64_t K, const void* A, int64_t lda, void* B,
-                       int64_t ldb, void* C, int64_t ldc, tsm_stream_t stream) {
+tsm_status tsm_gs_step_ex(tsm_dtype dtype, int M, int N, int64_t K, const void* A, int64_t lda, void* B,
+                          int64_t ldb, void* C, int64_t ldc, tsm_gs_mode mode, tsm_stream_t stream) {
     const double one[2] = {1.0, 0.0}, zero[2] = {0.0, 0.0}, minus_one[2] = {-1.0, 0.0};
     // every argument is checked before the first launch, so that an error
     // leaves B and C untouched
     tsm_status st = validate_common(dtype, M, N, K, one, zero);
     if (st != TSM_OK) return st;
+    if (mode != TSM_GS_AUTO && mode != TSM_GS_TWO_PRODUCTS && mode != TSM_GS_FUSED) return TSM_ERR_INVALID_VALUE;
     if (lda < M || ldb < N || ldc < N || !C) return TSM_ERR_INVALID_VALUE;
     if (K > 0 && (!A || !B)) return TSM_ERR_INVALID_VALUE;
     cudaStream_t s = (cudaStream_t)stream;
+    const bool fused = K > 0 && (mode == TSM_GS_FUSED || (mode == TSM_GS_AUTO && gs_fused_preferred(dtype, M, N, K)));
+    if (fused) {
+        if ((st = check_device()) != TSM_OK) return st;
+        return gs_fused_run(dtype, M, N, K, A, lda, B, ldb, C, ldc, s);
+    }
     if ((st = run_tsmttsm(TSM_OP_C, dtype, M, N, K, one, A, lda, B, ldb, zero, C, ldc, -1, 0, s)) != TSM_OK)
         return st;
     return run_tsmm(TSM_OP_N, dtype, M, N, K, minus_one, A, lda, C, ldc, one, B, ldb, -1, 0, s);
+}
+
+tsm_status tsm_gs_step(tsm_dtype dtype, int M, int N, int64_t K, const void* A, int64_t lda, void* B,
+                       int64_t ldb, void* C, int64_t ldc, tsm_stream_t stream) {
+    return tsm_gs_step_ex(dtype, M, N, K, A, lda, B, ldb, C, ldc, TSM_GS_AUTO, stream);
 }
 
 const char* tsm_status_string(tsm_status s) {

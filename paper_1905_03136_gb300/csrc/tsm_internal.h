@@ -139,8 +139,15 @@ struct Workspace {
     size_t partial_bytes;
     unsigned* tickets;
     int ticket_count;
+    unsigned gs_gen;  // barrier generation of the fused Gram-Schmidt kernel (gs_fused.cu)
 };
 tsm_status workspace_get(cudaStream_t stream, size_t partial_bytes, int tickets, Workspace** out);
+
+// The Gram-Schmidt step as one cooperative kernel (gs_fused.cu), and the
+// rule by which tsm_gs_step picks it over the two products.
+tsm_status gs_fused_run(tsm_dtype dtype, int M, int N, int64_t K, const void* A, int64_t lda, void* B,
+                        int64_t ldb, void* C, int64_t ldc, cudaStream_t s);
+bool gs_fused_preferred(tsm_dtype dtype, int M, int N, int64_t K);
 
 // Scale-only updates (K == 0 or alpha == 0 paths).
 cudaError_t launch_scale_small(double* C, int rows, int cols, int64_t ld, int cplx, double br,

@@ -42,7 +42,8 @@ def _orthonormal(K, M, cplx, ld=None):
 @pytest.mark.parametrize("cplx,M,N,ldpad", [(True, 8, 8, 0), (True, 32, 16, 3), (False, 64, 64, 0),
                                             (False, 5, 3, 2), (True, 1, 64, 0), (False, 64, 1, 1)],
                          ids=["c64-8x8", "c64-32x16-ld", "r64-64x64", "r64-5x3-ld", "c64-1x64", "r64-64x1-ld"])
-def test_gs_step_matches_oracle_and_orthogonalises(tsm, cplx, M, N, ldpad):
+@pytest.mark.parametrize("mode", ["two_products", "fused"])
+def test_gs_step_matches_oracle_and_orthogonalises(tsm, cplx, M, N, ldpad, mode):
     import torch
     K = (1 << 16) + 3
     Ap = _orthonormal(K, M, cplx, M + ldpad)
@@ -53,7 +54,7 @@ def test_gs_step_matches_oracle_and_orthogonalises(tsm, cplx, M, N, ldpad):
     dA = torch.from_numpy(Ap).cuda()[:, :M]
     dBp = torch.from_numpy(Bp).cuda()
     dB = dBp[:, :N]
-    C = tsm.gs_step(dA, dB)
+    C = tsm.gs_step(dA, dB, mode=mode)
     torch.cuda.synchronize()
     C_ref = oracle.gram(A, B0, op="C")
     assert oracle.rel_fro(C.cpu().numpy(), C_ref) <= TOL
@@ -108,3 +109,81 @@ def test_gs_step_twice_reorthogonalises(tsm):
     torch.cuda.synchronize()
     r = (torch.linalg.norm(C2) / torch.linalg.norm(C1)).item()
     assert r <= 1e-13, r
+
+
+@pytest.mark.parametrize("cplx,M,N", [(False, 1, 1), (True, 1, 1), (False, 17, 3), (True, 3, 17), (True, 64, 64),
+                                      (False, 64, 64), (False, 8, 8), (False, 63, 63), (True, 37, 53)])
+@pytest.mark.parametrize("K", [1, 31, 1000, (1 << 20) + 5])
+def test_gs_fused_matches_oracle_and_repeats(tsm, cplx, M, N, K):
+    """The fused kernel at row counts below, near and far above the grid
+    (fewer rows than CTAs, ragged ranges): C and B against the oracle, and
+    bit for bit the same on a second run from the same B."""
+    import torch
+    if K > 100000 and M * N > 64:
+        K = (1 << 17) + 5  # keeps the oracle's product within seconds
+    A = synth.block_vector(synth.SEED_A, K, M, complex_=cplx)
+    B0 = synth.block_vector(synth.SEED_B, K, N, complex_=cplx)
+    dA = torch.from_numpy(A).cuda()
+    outs = []
+    for _ in range(2):
+        dB = torch.from_numpy(B0).cuda()
+        C = tsm.gs_step(dA, dB, mode="fused")
+        torch.cuda.synchronize()
+        outs.append((C.cpu().numpy(), dB.cpu().numpy()))
+    tsm.gs_status()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    C_ref = oracle.gram(A, B0, op="C")
+    assert oracle.rel_fro(outs[0][0], C_ref) <= TOL
+    B_ref = oracle.apply(A, C_ref, alpha=-1.0, beta=1.0, B0=B0)
+    assert oracle.rel_fro(outs[0][1], B_ref) <= TOL
+
+
+def test_gs_fused_k0_sets_c_to_zero(tsm):
+    import torch
+    A = torch.zeros((0, 5), dtype=torch.complex128, device="cuda")
+    B = torch.zeros((0, 4), dtype=torch.complex128, device="cuda")
+    C = torch.full((5, 4), 3.0 + 1.0j, dtype=torch.complex128, device="cuda")
+    tsm.gs_step(A, B, C, mode="fused")
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(C).item() == 0
+
+
+def test_gs_fused_barrier_timeout_is_reported(tsm):
+    """A one-cycle barrier budget makes the waiting CTAs give up (no fault,
+    no hang: the last CTA to arrive still releases the barrier); the status
+    call reports TIMEOUT once, and the next step with the default budget is
+    correct again."""
+    import torch
+    from paper_1905_03136_gb300 import _lib
+    K, M, N = (1 << 18) + 3, 8, 8
+    A = synth.block_vector(synth.SEED_A, K, M)
+    B0 = synth.block_vector(synth.SEED_B, K, N)
+    dA = torch.from_numpy(A).cuda()
+    try:
+        tsm.gs_set_timeout(1)
+        tsm.gs_step(dA, torch.from_numpy(B0).cuda(), mode="fused")
+        with pytest.raises(_lib.TsmError) as e:
+            tsm.gs_status()
+        assert e.value.status == 5  # TSM_ERR_TIMEOUT
+        tsm.gs_status()  # the word was cleared
+    finally:
+        tsm.gs_set_timeout(0)
+    dB = torch.from_numpy(B0).cuda()
+    C = tsm.gs_step(dA, dB, mode="fused")
+    tsm.gs_status()
+    C_ref = oracle.gram(A, B0, op="C")
+    assert oracle.rel_fro(C.cpu().numpy(), C_ref) <= TOL
+    assert oracle.rel_fro(dB.cpu().numpy(), oracle.apply(A, C_ref, alpha=-1.0, beta=1.0, B0=B0)) <= TOL
+
+
+def test_gs_step_ex_rejects_unknown_mode(tsm):
+    import torch
+    lib = tsm.load()
+    A = torch.ones((100, 2), dtype=torch.float64, device="cuda")
+    B = torch.ones((100, 2), dtype=torch.float64, device="cuda")
+    C = torch.zeros((2, 2), dtype=torch.float64, device="cuda")
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.tsm_gs_step_ex(0, 2, 2, 100, ctypes.c_void_p(A.data_ptr()), 2, ctypes.c_void_p(B.data_ptr()), 2,
+                              ctypes.c_void_p(C.data_ptr()), 2, 7, s) == 1
+    torch.cuda.synchronize()
+    assert torch.all(B == 1.0).item()
