@@ -660,8 +660,11 @@ def run_e2e(calls, flatA, flatB, flatC, ideal_s, dev, K):
 def _reps_for(t_ideal_s):
     """Timed calls per point: several for calls below a millisecond, so that
     the host's launch latency of the first one (the start event is recorded
-    behind a single warm-up call) is spread over them; one above."""
-    return 1 if t_ideal_s > 1e-3 else 8
+    behind a single warm-up call, and that call cannot start before the
+    event) is spread over them -- 32 below 100 us, 8 below 1 ms; one above."""
+    if t_ideal_s > 1e-3:
+        return 1
+    return 8 if t_ideal_s > 1e-4 else 32
 
 
 def _time(fn, reps=3, warm=1):
