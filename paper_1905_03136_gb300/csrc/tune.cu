@@ -30,6 +30,7 @@ struct Entry {
     std::string name;
     int grid;
     float ms;
+    int index = -2;  // the variant's table index, resolved on first lookup (-1: no such variant)
 };
 typedef std::tuple<int, int, int, int, int> Key;
 
@@ -82,7 +83,7 @@ tsm_status tune_lookup(int kind, int dtype, int M, int N, int64_t K, int* varian
     }
     // exact K bucket first, then the nearest bucket tuned for this shape
     const int kb = k_bucket(K);
-    const Entry* best = nullptr;
+    Entry* best = nullptr;
     int best_d = 1 << 30;
     for (auto it = g_table.lower_bound(Key(kind, dtype, M, N, 0));
          it != g_table.end() && std::get<0>(it->first) == kind && std::get<1>(it->first) == dtype &&
@@ -95,7 +96,10 @@ tsm_status tune_lookup(int kind, int dtype, int M, int N, int64_t K, int* varian
         }
     }
     if (!best) return TSM_ERR_NOT_SUPPORTED;
-    const int v = find_variant(kind, best->name);
+    // the name is resolved once per entry: a scan of a few hundred variant
+    // names per call would cost microseconds of host time
+    if (best->index == -2) best->index = find_variant(kind, best->name);
+    const int v = best->index;
     if (v < 0) return TSM_ERR_NOT_SUPPORTED;
     *variant = v;
     *grid = best->grid;
