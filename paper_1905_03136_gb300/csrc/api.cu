@@ -8,6 +8,7 @@
 #include <mutex>
 #include <utility>
 
+#include "pdl_book.h"
 #include "tsm_internal.h"
 #include "tune.h"
 
@@ -136,26 +137,20 @@ bool pdl_allowed(const void* kernel, int grid, int block, size_t smem) {
 }
 
 Range operand_range(const void* p, int64_t rows, int64_t ld, int cols, int cplx) {
-    Range r = {0, 0};
-    if (!p || rows <= 0 || cols <= 0) return r;
-    r.lo = (uintptr_t)p;
-    r.hi = r.lo + (uintptr_t)(((uint64_t)(rows - 1) * (uint64_t)ld + (uint64_t)cols) * (cplx ? 16u : 8u));
-    return r;
+    const pdl::Span sp = pdl::operand_span(p, rows, ld, cols, cplx);
+    return Range{sp.lo, sp.hi};
 }
 
 namespace {
 
-bool overlaps(const Range& a, const Range& b) { return a.lo < b.hi && b.lo < a.hi; }
-
-// A fixed table (no allocation, so the no-allocation entry point can use
-// it); the least recently used record makes room for a new stream.
-constexpr int kPdlOuts = 8;
+// A fixed table of per-stream books (pdl_book.h; no allocation, so the
+// no-allocation entry point can use it); the least recently used record
+// makes room for a new stream.
 struct PdlRecord {
     int dev;
     cudaStream_t stream;
     unsigned long long used;
-    Range out[kPdlOuts];  // outputs since the last barrier, the barrier's first
-    int n;
+    pdl::Book book;
 };
 constexpr int kPdlRecords = 64;
 PdlRecord g_pdl[kPdlRecords];
@@ -177,11 +172,11 @@ int pdl_early(cudaStream_t s, const Range* in, int nin) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     const PdlRecord* r = pdl_find(dev, s);
-    if (!r || r->n >= kPdlOuts) return 0;
-    for (int j = 0; j < r->n; ++j)
-        for (int i = 0; i < nin; ++i)
-            if (overlaps(in[i], r->out[j])) return 0;
-    return 1;
+    if (!r) return 0;
+    pdl::Span sp[4];
+    if (nin > 4) return 0;
+    for (int i = 0; i < nin; ++i) sp[i] = pdl::Span{in[i].lo, in[i].hi};
+    return pdl::may_read_early(r->book, sp, nin);
 }
 
 void pdl_note(cudaStream_t s, Range out, int early) {
@@ -199,11 +194,11 @@ void pdl_note(cudaStream_t s, Range out, int early) {
         }
         r->dev = dev;
         r->stream = s;
-        early = 0;  // a new record starts at this product
+        r->book.valid = false;  // a new record starts at this product
+        r->book.n = 0;
     }
     r->used = ++g_pdl_clock;
-    if (!early || r->n >= kPdlOuts) r->n = 0;
-    r->out[r->n++] = out;
+    pdl::note_launch(r->book, pdl::Span{out.lo, out.hi}, early);
 }
 
 static tsm_status release_all() {
